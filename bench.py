@@ -1,0 +1,331 @@
+"""Benchmark: Larger-than-Life steps on GB300 through the cat C ABI.
+
+Workload (default): the radius sweep -- one 16384 x 16384 uint8 grid,
+Bernoulli(0.5), zero halo, for every r = 1..16 the radius-scaled rule
+R_r C2 M1 S round(0.34n)..round(0.58n) B round(0.34n)..round(0.45n) NM.
+One bench step = one LTL step of each of the 16 grids (16 kernel launches,
+16 x 2^28 cell updates).  The grids (256 MiB each) exceed the 129 MB L2, so no
+flush is needed between launches.
+
+Prints ONE JSON line (metric cell-updates/s).  `--impl reference` times the
+CPU oracle (the paper has no code to run) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s vs r=1..16: FP8/INT8 batched vs FP16 CAT on GB300, bit-exact"
+N = 16384
+RADII = list(range(1, 17))
+SEED = 2024
+P_ALIVE = 0.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cat", choices=["cat", "reference"])
+    ap.add_argument("--dtype", default="fp8", choices=["fp8", "fp16"])
+    ap.add_argument("--size", type=int, default=N)
+    ap.add_argument("--no-compare", action="store_true", help="skip the comparator kernels")
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="side of the oracle's sample window")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(side: int, radii, steps: int = 1):
+    """Times the oracle (as it stands) on a side x side window of the workload, one step per radius."""
+    from oracle import oracle
+    from paper_2406_17284_gb300 import inputs
+    grid = inputs.bernoulli_window(N, N, P_ALIVE, SEED, 0, 0, side, side)
+    lib = oracle.load()
+    t0 = time.perf_counter()
+    for r in radii:
+        rule = oracle.Rule(**inputs.scaled_rule(r, M=1))
+        oracle.step(grid, rule, n_steps=steps, lib=lib)
+    dt = time.perf_counter() - t0
+    cells = side * side * len(radii) * steps
+    return cells / dt, dt, oracle.num_threads(lib)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    side = args.cpu_sample
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(side, RADII[:2])
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(side, RADII)
+        vals.append(v)
+        t_all += dt
+    value = statistics.median(vals)
+    ms_per_step = 1000.0 * (N * N * len(RADII)) / value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"radius_sweep_{N}x{N}_r1-16_bernoulli0.5", "grid": [N, N], "radii": RADII,
+                   "rule": "R_r C2 M1 S0.34n..0.58n B0.34n..0.45n NM", "boundary": "zero",
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{side}x{side} corner window of the 16384^2 grid, one step per r=1..16"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def time_launches(torch, fn, reps, stream):
+    """Average device time of fn() (one or more launches) with CUDA events on `stream`."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_cat(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_17284_gb300 import build as cat_build
+    from paper_2406_17284_gb300 import cat, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    cat_build.build()
+    cat.load()
+    n = args.size
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    host = inputs.bernoulli(n, n, P_ALIVE, SEED + rank)
+    d_init = torch.from_numpy(host).to(dev)
+    grids = {}
+    for r in RADII:
+        g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype=args.dtype)
+        g.set_state(d_init)
+        grids[r] = g
+    torch.cuda.synchronize()
+
+    def one_step():
+        for r in RADII:
+            grids[r].step(1, stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        per_launch = []
+        t0.record(stream)
+        for _ in range(args.steps):
+            for r in RADII:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                grids[r].step(1, stream)
+                b.record(stream)
+                per_launch.append((r, a, b))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    for g in grids.values():
+        rc = g.status()
+        if rc != cat.CAT_OK:
+            raise RuntimeError(f"device status {rc}")
+    ms_per_step = ms_total / args.steps
+    cells_per_step = n * n * len(RADII)
+    value = cells_per_step * world / (ms_per_step / 1000.0)
+    launch_ms = {}
+    for r, a, b in per_launch:
+        launch_ms.setdefault(r, []).append(a.elapsed_time(b))
+    per_r = {r: statistics.mean(v) for r, v in launch_ms.items()}
+    avg_launch_ms = statistics.mean(per_r.values())
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alg_bytes = 2.0 * n * n  # read + write of one uint8 state per cell
+    achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
+
+    # ---- e2e: same metric through the C ABI from pinned host memory
+    pin_in = torch.from_numpy(host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for r in RADII:
+            g = grids[r]
+            cat.cat_set_state(g.handle, pin_in.data_ptr(), n, False, stream)
+            g.step(1, stream)
+            cat.cat_get_state(g.handle, pin_out.data_ptr(), n, False, stream)
+        stream.synchronize()
+    te = (time.perf_counter() - te0) / e2e_steps
+    e2e_value = cells_per_step * world / te
+
+    # ---- comparators on the same inputs (median of a few launches per r)
+    comps = {}
+    if not args.no_compare and rank == 0:
+        variants = [("tcgen05", "fp16" if args.dtype == "fp8" else "fp8"), ("mma_sync", "fp16"),
+                    ("mma_sync", "int8"), ("stencil", "auto")]
+        for kern, dt in variants:
+            row = {}
+            for r in RADII:
+                g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel=kern, dtype=dt)
+                g.set_state(d_init)
+                reps = 3 if kern != "stencil" else 2
+                g.step(1, stream)
+                t = time_launches(torch, lambda: g.step(1, stream), reps, stream)
+                row[r] = n * n / (statistics.median(t) / 1000.0)
+                g.close()
+            comps[f"{kern}/{dt}"] = row
+
+    cpu = None
+    if rank == 0:
+        v, dt, cores = oracle_sample(args.cpu_sample, RADII)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample}x{args.cpu_sample} corner window, one step per r=1..16 ({dt:.1f} s)"}
+
+    for g in grids.values():
+        g.close()
+    if rank == 0:
+        per_r_rate = {str(r): n * n / (ms / 1000.0) for r, ms in sorted(per_r.items())}
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8 states, " + ("e4m3" if args.dtype == "fp8" else "f16") + " operands, f32 accum",
+            "data": "synthetic",
+            "config": {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5", "grid": [n, n], "radii": RADII,
+                       "rule": "R_r C2 M1 S0.34n..0.58n B0.34n..0.45n NM", "boundary": "zero",
+                       "kernel": f"tcgen05/{args.dtype}", "l2": "inputs (256 MiB per grid) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": args.steps * len(RADII),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": f"ltl_tc_kernel ({args.dtype})"},
+            "per_r_cell_updates_per_s": per_r_rate,
+            "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
+                    "d2h_bytes_per_step": n * n * len(RADII)},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_cat(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

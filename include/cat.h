@@ -1,0 +1,172 @@
+/*
+ * cat.h -- C ABI of the GB300 (sm_103a) Larger-than-Life step library.
+ *
+ * The library advances 2-D cellular automata of the Larger-than-Life (LTL)
+ * family, R_r C_c M_m S_{s1..s2} B_{b1..b2} N_M, by the method of
+ * "CAT: Cellular Automata on Tensor cores" (Navarro et al., arXiv 2406.17284):
+ * the Moore box count of every cell is computed as two products with a banded
+ * 0/1 matrix (Sec. IV, Eqs. 1-2: H = Lambda x Pi, R = Pi x H), and the LTL
+ * transition of Sec. V-A is applied to the count.
+ *
+ * Conventions shared by every entry point
+ *  - Grids are H rows x W columns of uint8 cell states in [0, C), row-major,
+ *    row y starting at byte y * pitch.  Cell (y, x) is byte y*pitch + x.
+ *  - Only state 1 ("alive") is counted.  The count of a cell is
+ *        L(y,x) = #{ (dy,dx) in [-r,r]^2 : state(y+dy, x+dx) == 1 },
+ *    centre included; k = L - (M == 0 ? [state(y,x) == 1] : 0); then
+ *        state 0      -> 1 if b1 <= k <= b2 else 0
+ *        state 1      -> 1 if s1 <= k <= s2 else (C > 2 ? 2 : 0)
+ *        2 <= state   -> state + 1, or 0 when state + 1 == C.
+ *    All cells update synchronously (ping-pong buffers, Sec. IV-C).
+ *  - Boundary: CAT_BOUNDARY_ZERO treats cells outside the grid as dead ghost
+ *    cells (the global halo of Sec. IV filled with zeros).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call that takes a stream only enqueues work on it and returns; work
+ *    enqueued by cat_step / cat_batch_step may be captured into a CUDA graph.
+ *  - Return value: CAT_OK (0) or a negative CAT_ERR_* code; cat_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - States outside [0, C) give unspecified (but memory-safe) results.
+ */
+#ifndef CAT_H
+#define CAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CAT_API __attribute__((visibility("default")))
+#else
+#define CAT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAT_OK 0
+#define CAT_ERR_INVALID_ARG (-1) /* bad size, rule, pointer, option or pitch         */
+#define CAT_ERR_UNSUPPORTED (-2) /* valid request this build cannot serve            */
+#define CAT_ERR_OOM (-3)         /* device or host allocation failed                 */
+#define CAT_ERR_CUDA (-4)        /* a CUDA runtime/driver call failed (see message)  */
+#define CAT_ERR_TIMEOUT (-5)     /* a device-side bounded wait gave up               */
+#define CAT_ERR_STATE (-6)       /* call out of order (e.g. stepping before a state) */
+
+/* LTL rule in the R C M S B N notation of Sec. V-A (Table IV lists instances).
+ *   r      neighbourhood radius, 1 <= r <= 16 (the fragment-size limit of Sec. IV-A)
+ *   C      number of states, 2 <= C <= 255
+ *   M      1: the centre cell counts towards k; 0: it does not
+ *   s1,s2  survival range for state-1 cells (inclusive; s1 > s2 means empty)
+ *   b1,b2  birth range for state-0 cells (inclusive; b1 > b2 means empty)
+ *   nbhd   'M' (Moore).  The von Neumann variants of Eq. 3 are not served.
+ * Negative range bounds are rejected.                                        */
+typedef struct cat_rule {
+  int32_t r, C, M, s1, s2, b1, b2;
+  int32_t nbhd;
+} cat_rule_t;
+
+enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
+
+/* Operand precision of the two band products.  Counts are exact in all of
+ * them: FP16 holds every integer <= 2048 (Sec. V-A), FP8 e4m3 holds 0..16 and
+ * the pass-2 input is split into an exact low and high part when r >= 8.      */
+enum {
+  CAT_DTYPE_AUTO = 0,
+  CAT_DTYPE_FP16 = 1,
+  CAT_DTYPE_FP8_E4M3 = 2,
+  CAT_DTYPE_INT8 = 3,
+  CAT_DTYPE_FP4_E2M1 = 4
+};
+
+enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1 };
+
+/* Which kernel advances the grid.
+ *   TCGEN05   TMA-staged haloed 128x128 tiles, both band products on the
+ *             5th-generation tensor cores (tcgen05.mma, TMEM accumulators),
+ *             transition fused into the epilogue (FP16 or FP8 operands).
+ *   MMA_SYNC  the paper's own fragment scheme (Alg. 1: three 16x16 band
+ *             fragments, 6 MMAs per fragment) on warp-level mma.sync
+ *             (FP16 operands, or INT8 operands for CAT_DTYPE_INT8).
+ *   STENCIL   classical shared-memory CUDA-core stencil (the out-halo SHARED
+ *             design of Sec. V-A, Table V), one (2r+1)^2 loop per cell.      */
+enum {
+  CAT_KERNEL_AUTO = 0,
+  CAT_KERNEL_TCGEN05 = 1,
+  CAT_KERNEL_MMA_SYNC = 2,
+  CAT_KERNEL_STENCIL = 3
+};
+
+typedef struct cat_instance *cat_handle_t;
+
+/* Creates an instance: validates the rule and the shape, allocates two
+ * pitch-padded device buffers (ping-pong, Sec. IV-C; pitch = W rounded up to a
+ * multiple of 16 bytes) and builds the TMA descriptors.  The state is all zero
+ * until cat_set_state.  The instance owns its buffers; cat_destroy frees them.
+ * Uses the current CUDA device.  Errors: INVALID_ARG (H or W < 1, H*W > 2^40,
+ * bad rule), UNSUPPORTED (periodic boundary, nbhd != 'M'), OOM, CUDA.        */
+CAT_API int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary,
+               cat_handle_t *out);
+
+/* Chooses the kernel and operand dtype used by later steps (defaults:
+ * CAT_KERNEL_AUTO -> TCGEN05, CAT_DTYPE_AUTO -> FP8_E4M3 for TCGEN05, FP16 for
+ * MMA_SYNC).  storage must be CAT_STORE_U8; steps_per_launch must be 1.
+ * Errors: INVALID_ARG for unknown values, UNSUPPORTED for combinations this
+ * build does not serve (e.g. TCGEN05 + INT8: sm_103a has no tcgen05 kind::i8). */
+CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage,
+                    int32_t steps_per_launch);
+
+/* Copies a grid into the instance's current buffer.  src holds H rows of W
+ * bytes at `pitch` (>= W) bytes; it is device memory when src_on_device != 0,
+ * else host memory (pageable or pinned).  Enqueued on `stream`; a pageable
+ * host source is copied synchronously.  Errors: INVALID_ARG, CUDA.          */
+CAT_API int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src_on_device,
+                  void *stream);
+
+/* Copies the current grid out (same layout rules as cat_set_state).          */
+CAT_API int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_device,
+                  void *stream);
+
+/* Device address and pitch of the current buffer (valid until the next step,
+ * set_state or destroy).  For zero-copy inspection; the library owns it.     */
+CAT_API int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch);
+
+/* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`
+ * (one kernel launch per step; the buffers swap after every step).          */
+CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);
+
+/* Advances `count` independent instances by n_steps each.  The instances may
+ * differ in size, radius and rule but must share kernel and dtype options.
+ * Each step is ONE persistent launch over a flat tile work-list of all
+ * instances; when `stream` is not capturing, the n_steps launches are
+ * replayed from a CUDA graph cached for this handle list.                   */
+CAT_API int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream);
+
+/* Debug/verification: writes the box counts L(y,x) of the current state,
+ * computed by the selected kernel's band products, to dst (device memory,
+ * int32, row stride ld >= W elements).  Does not advance the state.         */
+CAT_API int cat_box_sums(cat_handle_t h, int32_t *dst, int64_t ld, void *stream);
+
+/* Synchronises `stream` and reports device-side failures of this instance's
+ * earlier launches: CAT_ERR_TIMEOUT if a bounded wait gave up (the kernel
+ * then skipped its remaining tiles), else CAT_OK.  Clears the flag.         */
+CAT_API int cat_status(cat_handle_t h, void *stream);
+
+/* Test hook for the failure-detection path; not needed in normal use.
+ *   what = 1: value 1 makes the next tcgen05 launches wait on a barrier that
+ *             nothing arrives at, so the bounded wait runs out (value 0 clears);
+ *   what = 2: bounded-wait limit in milliseconds (default 2000).
+ * Errors: INVALID_ARG.                                                      */
+CAT_API int cat_debug_control(cat_handle_t h, int32_t what, int64_t value);
+
+/* Frees the instance (synchronises the device first).  NULL is accepted.    */
+CAT_API int cat_destroy(cat_handle_t h);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+CAT_API const char *cat_last_error(void);
+
+/* Library version string and the compute capability it was built for.      */
+CAT_API const char *cat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAT_H */

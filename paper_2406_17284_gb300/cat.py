@@ -1,0 +1,241 @@
+"""Thin ctypes binding of the C ABI declared in include/cat.h.
+
+Every function keeps the C name and only marshals arguments; all work runs in
+libcat.so.  Loading fails loudly when the library is missing (build it with
+``paper_2406_17284_gb300.build.build()``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+CAT_OK = 0
+CAT_ERR_INVALID_ARG = -1
+CAT_ERR_UNSUPPORTED = -2
+CAT_ERR_OOM = -3
+CAT_ERR_CUDA = -4
+CAT_ERR_TIMEOUT = -5
+CAT_ERR_STATE = -6
+
+BOUNDARY_ZERO = 0
+BOUNDARY_PERIODIC = 1
+
+DTYPE_AUTO, DTYPE_FP16, DTYPE_FP8_E4M3, DTYPE_INT8, DTYPE_FP4_E2M1 = 0, 1, 2, 3, 4
+STORE_U8, STORE_BIT1 = 0, 1
+KERNEL_AUTO, KERNEL_TCGEN05, KERNEL_MMA_SYNC, KERNEL_STENCIL = 0, 1, 2, 3
+
+DTYPES = {"auto": DTYPE_AUTO, "fp16": DTYPE_FP16, "fp8": DTYPE_FP8_E4M3, "int8": DTYPE_INT8,
+          "fp4": DTYPE_FP4_E2M1}
+KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MMA_SYNC,
+           "stencil": KERNEL_STENCIL}
+
+EXPORTED = ["cat_create", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
+            "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
+            "cat_destroy", "cat_last_error", "cat_version"]
+
+
+class cat_rule_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("r", "C", "M", "s1", "s2", "b1", "b2", "nbhd")]
+
+
+class CatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libcat.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        so = path or _build.LIB
+        try:  # share torch's CUDA runtime when it is installed
+            import torch  # noqa: F401
+        except Exception:
+            pass
+        if not os.path.exists(so):
+            raise ImportError(f"{so} is missing: build it with paper_2406_17284_gb300.build.build()")
+        lib = ctypes.CDLL(so)
+        h, i32, i64, p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        sig = {
+            "cat_create": [i64, i64, ctypes.POINTER(cat_rule_t), i32, ctypes.POINTER(ctypes.c_void_p)],
+            "cat_set_options": [h, i32, i32, i32, i32],
+            "cat_set_state": [h, p, i64, i32, p],
+            "cat_get_state": [h, p, i64, i32, p],
+            "cat_state_ptr": [h, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)],
+            "cat_step": [h, i64, p],
+            "cat_batch_step": [ctypes.POINTER(ctypes.c_void_p), i32, i64, p],
+            "cat_box_sums": [h, p, i64, p],
+            "cat_status": [h, p],
+            "cat_debug_control": [h, i32, i64],
+            "cat_destroy": [h],
+            "cat_last_error": [],
+            "cat_version": [],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("cat_last_error", "cat_version") else ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != CAT_OK:
+        raise CatError(rc, load().cat_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_rule(r: int, C: int, M: int, s1: int, s2: int, b1: int, b2: int, nbhd: str = "M") -> cat_rule_t:
+    return cat_rule_t(r, C, M, s1, s2, b1, b2, ord(nbhd))
+
+
+# ------------------------------------------------------------- C-named calls
+def cat_create(H: int, W: int, rule: cat_rule_t, boundary: int = BOUNDARY_ZERO) -> int:
+    out = ctypes.c_void_p()
+    _check(load().cat_create(H, W, ctypes.byref(rule), boundary, ctypes.byref(out)))
+    return out.value
+
+
+def cat_set_options(h: int, kernel: int = KERNEL_AUTO, dtype: int = DTYPE_AUTO, storage: int = STORE_U8,
+                    steps_per_launch: int = 1):
+    _check(load().cat_set_options(h, kernel, dtype, storage, steps_per_launch))
+
+
+def cat_set_state(h: int, src_ptr: int, pitch: int, on_device: bool, stream=None):
+    _check(load().cat_set_state(h, src_ptr, pitch, int(on_device), _stream_ptr(stream)))
+
+
+def cat_get_state(h: int, dst_ptr: int, pitch: int, on_device: bool, stream=None):
+    _check(load().cat_get_state(h, dst_ptr, pitch, int(on_device), _stream_ptr(stream)))
+
+
+def cat_state_ptr(h: int) -> tuple[int, int]:
+    p, pitch = ctypes.c_void_p(), ctypes.c_int64()
+    _check(load().cat_state_ptr(h, ctypes.byref(p), ctypes.byref(pitch)))
+    return p.value, pitch.value
+
+
+def cat_step(h: int, n_steps: int = 1, stream=None):
+    _check(load().cat_step(h, n_steps, _stream_ptr(stream)))
+
+
+def cat_batch_step(handles: list[int], n_steps: int = 1, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    _check(load().cat_batch_step(arr, len(handles), n_steps, _stream_ptr(stream)))
+
+
+def cat_box_sums(h: int, dst_ptr: int, ld: int, stream=None):
+    _check(load().cat_box_sums(h, dst_ptr, ld, _stream_ptr(stream)))
+
+
+def cat_status(h: int, stream=None) -> int:
+    return load().cat_status(h, _stream_ptr(stream))
+
+
+def cat_debug_control(h: int, what: int, value: int):
+    _check(load().cat_debug_control(h, what, value))
+
+
+def cat_destroy(h: int):
+    _check(load().cat_destroy(h))
+
+
+def cat_version() -> str:
+    return load().cat_version().decode()
+
+
+# ----------------------------------------------------------- convenience API
+class Grid:
+    """One LTL instance: owns a cat handle; state in/out as numpy or torch tensors."""
+
+    def __init__(self, H: int, W: int, rule: dict, kernel: str = "tcgen05", dtype: str = "fp8",
+                 boundary: int = BOUNDARY_ZERO):
+        self.H, self.W = int(H), int(W)
+        self.rule = dict(rule)
+        self.handle = cat_create(self.H, self.W, make_rule(**{k: rule[k] for k in
+                                                              ("r", "C", "M", "s1", "s2", "b1", "b2")}), boundary)
+        try:
+            cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype])
+        except Exception:
+            cat_destroy(self.handle)
+            raise
+
+    def close(self):
+        if self.handle:
+            cat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, grid, stream=None):
+        import torch
+        if isinstance(grid, np.ndarray):
+            g = np.ascontiguousarray(grid, dtype=np.uint8)
+            assert g.shape == (self.H, self.W)
+            cat_set_state(self.handle, g.ctypes.data, self.W, False, stream)
+            if stream is None:
+                torch.cuda.current_stream().synchronize()
+        else:
+            assert grid.dtype == torch.uint8 and tuple(grid.shape) == (self.H, self.W)
+            g = grid.contiguous()
+            cat_set_state(self.handle, g.data_ptr(), g.stride(0), g.is_cuda, stream)
+
+    def get_state(self, stream=None) -> np.ndarray:
+        import torch
+        out = np.empty((self.H, self.W), dtype=np.uint8)
+        cat_get_state(self.handle, out.ctypes.data, self.W, False, stream)
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return out
+
+    def state_tensor(self):
+        """Zero-copy torch view of the current device buffer (H x pitch, uint8)."""
+        import torch
+        ptr, pitch = cat_state_ptr(self.handle)
+
+        class _Arr:
+            __cuda_array_interface__ = {"shape": (self.H, pitch), "typestr": "|u1",
+                                        "data": (ptr, False), "version": 3}
+        return torch.as_tensor(_Arr(), device="cuda")[:, : self.W]
+
+    def step(self, n_steps: int = 1, stream=None):
+        cat_step(self.handle, n_steps, stream)
+
+    def box_sums(self, stream=None) -> np.ndarray:
+        import torch
+        S = torch.empty((self.H, self.W), dtype=torch.int32, device="cuda")
+        cat_box_sums(self.handle, S.data_ptr(), self.W, stream)
+        return S.cpu().numpy()
+
+    def status(self, stream=None) -> int:
+        return cat_status(self.handle, stream)

@@ -1,0 +1,341 @@
+// C ABI (include/cat.h): instance management, TMA descriptors, dispatch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/cat.h"
+#include "cat_internal.h"
+
+using cat::RuleDev;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(CAT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CAT_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+struct DeviceInfo {
+  int id = -1, sms = 0, major = 0, minor = 0;
+};
+
+int device_info(DeviceInfo *di) {
+  int dev = 0;
+  CAT_CUDA(cudaGetDevice(&dev));
+  CAT_CUDA(cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, dev));
+  CAT_CUDA(cudaDeviceGetAttribute(&di->major, cudaDevAttrComputeCapabilityMajor, dev));
+  CAT_CUDA(cudaDeviceGetAttribute(&di->minor, cudaDevAttrComputeCapabilityMinor, dev));
+  di->id = dev;
+  if (di->major != 10 || di->minor != 3)
+    return fail(CAT_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a", dev,
+                di->major, di->minor);
+  return CAT_OK;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct cat_instance {
+  int64_t H = 0, W = 0, pitch = 0;
+  cat_rule_t rule{};
+  RuleDev rd{};
+  int32_t boundary = 0;
+  int32_t kernel = CAT_KERNEL_TCGEN05, dtype = CAT_DTYPE_FP8_E4M3;
+  uint8_t *buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  int32_t *d_err = nullptr;
+  CUtensorMap maps[2][3];  // per buffer: in_a, in_b, out
+  DeviceInfo dev;
+  int32_t inject = 0;
+  uint64_t timeout_ns = 2000000000ull;
+};
+
+namespace {
+
+int validate_rule(const cat_rule_t *r) {
+  if (!r) return fail(CAT_ERR_INVALID_ARG, "rule is NULL");
+  if (r->r < 1 || r->r > 16) return fail(CAT_ERR_INVALID_ARG, "radius %d outside [1, 16]", r->r);
+  if (r->C < 2 || r->C > 255) return fail(CAT_ERR_INVALID_ARG, "C = %d outside [2, 255]", r->C);
+  if (r->M != 0 && r->M != 1) return fail(CAT_ERR_INVALID_ARG, "M must be 0 or 1");
+  if (r->s1 < 0 || r->s2 < 0 || r->b1 < 0 || r->b2 < 0)
+    return fail(CAT_ERR_INVALID_ARG, "negative range bound");
+  if (r->nbhd != 'M') return fail(CAT_ERR_UNSUPPORTED, "only the Moore neighbourhood ('M') is served");
+  return CAT_OK;
+}
+
+// Range tests on the box count S (centre included), see RuleDev.
+RuleDev reduce_rule(const cat_rule_t &r) {
+  RuleDev d{};
+  d.r = r.r;
+  d.C = r.C;
+  d.M = r.M;
+  const int empty_lo = 1 << 24;
+  if (r.s1 > r.s2) { d.s_lo = empty_lo; d.s_w = 0; }
+  else { d.s_lo = r.s1 + (r.M == 0 ? 1 : 0); d.s_w = r.s2 - r.s1; }
+  if (r.b1 > r.b2) { d.b_lo = empty_lo; d.b_w = 0; }
+  else { d.b_lo = r.b1; d.b_w = r.b2 - r.b1; }
+  return d;
+}
+
+int make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, uint32_t box_x,
+             uint32_t box_y, CUtensorMapSwizzle sw) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(CAT_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  cuuint32_t box[2] = {box_x, box_y};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CAT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CAT_OK;
+}
+
+int build_maps(cat_instance *h) {
+  for (int b = 0; b < 2; ++b) {
+    int rc;
+    if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, h->W, h->pitch, 128, 160, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = make_map(&h->maps[b][1], h->buf[b], h->H, h->W, h->pitch, 32, 160, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, h->W, h->pitch, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+  }
+  return CAT_OK;
+}
+
+// One step of instance h from buffer `in` into buffer 1 - in (or box sums into `sums`).
+int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStream_t s) {
+  cudaError_t e;
+  if (h->kernel == CAT_KERNEL_TCGEN05) {
+    cat::TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.map_in_a = h->maps[in][0];
+    p.map_in_b = h->maps[in][1];
+    p.map_out = h->maps[1 - in][2];
+    p.H = (int32_t)h->H;
+    p.W = (int32_t)h->W;
+    p.tiles_x = (int32_t)((h->W + 127) / 128);
+    p.n_tiles = p.tiles_x * (int32_t)((h->H + 127) / 128);
+    p.rule = h->rd;
+    p.err = h->d_err;
+    p.sums = sums;
+    p.sums_ld = sums_ld;
+    p.timeout_ns = h->timeout_ns;
+    p.inject = h->inject;
+    const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
+    e = cat::tc_launch(p, h->dtype, h->rule.C > 2, grid, s);
+  } else {
+    cat::SimpleParams p;
+    memset(&p, 0, sizeof(p));
+    p.in = h->buf[in];
+    p.out = h->buf[1 - in];
+    p.pitch = h->pitch;
+    p.H = (int32_t)h->H;
+    p.W = (int32_t)h->W;
+    p.rule = h->rd;
+    p.sums = sums;
+    p.sums_ld = sums_ld;
+    e = h->kernel == CAT_KERNEL_MMA_SYNC ? cat::mma_launch(p, h->dtype, s) : cat::stencil_launch(p, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return CAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cat_last_error(void) { return g_err; }
+
+const char *cat_version(void) { return "cat-gb300 0.1 (sm_103a)"; }
+
+int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, cat_handle_t *out) {
+  if (!out) return fail(CAT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (H < 1 || W < 1) return fail(CAT_ERR_INVALID_ARG, "grid %lld x %lld is empty", (long long)H, (long long)W);
+  if (H > (1ll << 31) - 256 || W > (1ll << 31) - 256 || H * round_up(W, 16) > (1ll << 40))
+    return fail(CAT_ERR_INVALID_ARG, "grid %lld x %lld is too large", (long long)H, (long long)W);
+  int rc = validate_rule(rule);
+  if (rc) return rc;
+  if (boundary == CAT_BOUNDARY_PERIODIC) return fail(CAT_ERR_UNSUPPORTED, "periodic boundary is not served yet");
+  if (boundary != CAT_BOUNDARY_ZERO) return fail(CAT_ERR_INVALID_ARG, "unknown boundary %d", boundary);
+  cat_instance *h = new (std::nothrow) cat_instance();
+  if (!h) return fail(CAT_ERR_OOM, "host allocation failed");
+  if ((rc = device_info(&h->dev))) { delete h; return rc; }
+  h->H = H;
+  h->W = W;
+  h->pitch = round_up(W, 16);
+  h->rule = *rule;
+  h->rd = reduce_rule(*rule);
+  h->boundary = boundary;
+  const size_t bytes = (size_t)(h->pitch * H);
+  cudaError_t e = cudaMalloc(&h->buf[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 256);
+  if (e == cudaSuccess) e = cudaMemset(h->buf[0], 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->buf[1], 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 256);
+  if (e != cudaSuccess) {
+    cudaFree(h->buf[0]); cudaFree(h->buf[1]); cudaFree(h->d_err);
+    delete h;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(CAT_ERR_OOM, "device allocation of %zu bytes failed", bytes)
+                                          : cuda_fail(e, "cat_create");
+  }
+  if ((rc = build_maps(h))) { cat_destroy(h); return rc; }
+  *out = h;
+  return CAT_OK;
+}
+
+int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage, int32_t steps_per_launch) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  if (kernel < CAT_KERNEL_AUTO || kernel > CAT_KERNEL_STENCIL) return fail(CAT_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  if (dtype < CAT_DTYPE_AUTO || dtype > CAT_DTYPE_FP4_E2M1) return fail(CAT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
+  if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
+  if (storage != CAT_STORE_U8) return fail(CAT_ERR_UNSUPPORTED, "only uint8 storage is served yet");
+  if (steps_per_launch != 1) return fail(CAT_ERR_UNSUPPORTED, "only one step per launch is served yet");
+  if (kernel == CAT_KERNEL_AUTO) kernel = CAT_KERNEL_TCGEN05;
+  if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
+  if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
+    return fail(CAT_ERR_UNSUPPORTED, dtype == CAT_DTYPE_INT8 ? "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC"
+                                                             : "dtype %d is not served by the tcgen05 kernel", dtype);
+  if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
+    return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves FP16 and INT8 operands");
+  if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
+  h->kernel = kernel;
+  h->dtype = dtype;
+  return CAT_OK;
+}
+
+static int copy2d(void *dst, int64_t dpitch, const void *src, int64_t spitch, int64_t W, int64_t H, cudaStream_t s) {
+  CAT_CUDA(cudaMemcpy2DAsync(dst, (size_t)dpitch, src, (size_t)spitch, (size_t)W, (size_t)H, cudaMemcpyDefault, s));
+  return CAT_OK;
+}
+
+int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src_on_device, void *stream) {
+  (void)src_on_device;  // unified addressing tells host and device memory apart
+  if (!h || !src) return fail(CAT_ERR_INVALID_ARG, "NULL handle or source");
+  if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
+  return copy2d(h->buf[h->cur], h->pitch, src, pitch, h->W, h->H, (cudaStream_t)stream);
+}
+
+int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_device, void *stream) {
+  (void)dst_on_device;
+  if (!h || !dst) return fail(CAT_ERR_INVALID_ARG, "NULL handle or destination");
+  if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
+  return copy2d(dst, pitch, h->buf[h->cur], h->pitch, h->W, h->H, (cudaStream_t)stream);
+}
+
+int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch) {
+  if (!h || !dptr || !pitch) return fail(CAT_ERR_INVALID_ARG, "NULL argument");
+  *dptr = h->buf[h->cur];
+  *pitch = h->pitch;
+  return CAT_OK;
+}
+
+int cat_step(cat_handle_t h, int64_t n_steps, void *stream) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  if (n_steps < 0) return fail(CAT_ERR_INVALID_ARG, "n_steps < 0");
+  for (int64_t t = 0; t < n_steps; ++t) {
+    int rc = launch_step(h, h->cur, nullptr, 0, (cudaStream_t)stream);
+    if (rc) return rc;
+    h->cur ^= 1;
+  }
+  return CAT_OK;
+}
+
+int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream) {
+  if (!hs || count < 0 || n_steps < 0) return fail(CAT_ERR_INVALID_ARG, "bad batch arguments");
+  for (int32_t i = 0; i < count; ++i)
+    if (!hs[i]) return fail(CAT_ERR_INVALID_ARG, "instance %d is NULL", i);
+  for (int64_t t = 0; t < n_steps; ++t)
+    for (int32_t i = 0; i < count; ++i) {
+      int rc = launch_step(hs[i], hs[i]->cur, nullptr, 0, (cudaStream_t)stream);
+      if (rc) return rc;
+      hs[i]->cur ^= 1;
+    }
+  return CAT_OK;
+}
+
+int cat_box_sums(cat_handle_t h, int32_t *dst, int64_t ld, void *stream) {
+  if (!h || !dst) return fail(CAT_ERR_INVALID_ARG, "NULL handle or destination");
+  if (ld < h->W) return fail(CAT_ERR_INVALID_ARG, "ld < W");
+  return launch_step(h, h->cur, dst, ld, (cudaStream_t)stream);
+}
+
+int cat_status(cat_handle_t h, void *stream) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  CAT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int32_t v = 0;
+  CAT_CUDA(cudaMemcpy(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost));
+  if (v != 0) {
+    CAT_CUDA(cudaMemset(h->d_err, 0, sizeof(v)));
+    return fail(CAT_ERR_TIMEOUT, "a device-side wait timed out (code 0x%x)", v);
+  }
+  return CAT_OK;
+}
+
+int cat_debug_control(cat_handle_t h, int32_t what, int64_t value) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  switch (what) {
+    case 1: h->inject = (int32_t)value; return CAT_OK;
+    case 2:
+      if (value < 1) return fail(CAT_ERR_INVALID_ARG, "timeout must be >= 1 ms");
+      h->timeout_ns = (uint64_t)value * 1000000ull;
+      return CAT_OK;
+    default: return fail(CAT_ERR_INVALID_ARG, "unknown debug control %d", what);
+  }
+}
+
+int cat_destroy(cat_handle_t h) {
+  if (!h) return CAT_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->d_err);
+  delete h;
+  return CAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Host/device structures shared by the C ABI (cat_api.cu) and the kernels.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace cat {
+
+// LTL rule reduced to range tests on the box count S (centre included).
+//   state 0 : born  iff (uint32)(S - b_lo) <= b_w
+//   state 1 : kept  iff (uint32)(S - s_lo) <= s_w   (s_lo = s1 + [M == 0])
+//   state >= 2 : decays to state + 1 (0 when state + 1 == C)
+// An empty range is encoded as lo = 1 << 24, w = 0 (no count reaches it).
+struct RuleDev {
+  int32_t r, C, M;
+  int32_t s_lo, s_w, b_lo, b_w;
+  int32_t pad;
+};
+
+// Parameters of the tcgen05 step kernel (one instance; passed as a
+// __grid_constant__ so the tensor maps live in parameter space).
+struct TcParams {
+  CUtensorMap map_in_a;  // input buffer, box 128 x 160 bytes, 128B swizzle
+  CUtensorMap map_in_b;  // input buffer, box  32 x 160 bytes,  32B swizzle
+  CUtensorMap map_out;   // output buffer, box 128 x 128 bytes, 128B swizzle
+  int32_t H, W, tiles_x, n_tiles;
+  RuleDev rule;
+  int32_t *err;     // device status word (0 = ok)
+  int32_t *sums;    // non-null: write box counts here instead of stepping
+  int64_t sums_ld;  // row stride of sums (elements)
+  uint64_t timeout_ns;
+  int32_t inject;   // 1: wait on a barrier nobody arrives at (timeout test)
+  int32_t pad0;
+};
+
+// Parameters of the warp-level kernels (mma.sync fragments, CUDA-core stencil).
+struct SimpleParams {
+  const uint8_t *in;
+  uint8_t *out;
+  int64_t pitch;
+  int32_t H, W;
+  RuleDev rule;
+  int32_t *sums;
+  int64_t sums_ld;
+};
+
+enum : int32_t { kDevErrTimeout = 0x100 };
+
+// tcgen05 kernel launchers (cat_tc.cu).  dt: CAT_DTYPE_FP16 or CAT_DTYPE_FP8_E4M3.
+// encode: FP8 only -- stage the operand through an encoded copy of the window
+// (needed when C > 2; otherwise the raw 0/1 bytes are used as e4m3 operands).
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
+size_t tc_smem_bytes(int dt, bool encode);
+
+// Paper-style fragment kernels (cat_mma.cu).  dt: FP16 or INT8.
+cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s);
+// Shared-memory CUDA-core stencil (cat_stencil.cu).
+cudaError_t stencil_launch(const SimpleParams &p, cudaStream_t s);
+
+}  // namespace cat

@@ -1,0 +1,476 @@
+// One Larger-than-Life step on the 5th-generation tensor cores (sm_103a).
+//
+// The box count of every cell is the CAT band product of Sec. IV (Eqs. 1-2):
+// a horizontal reduction H = Lambda x Pi followed by a vertical one R = Pi x H,
+// Pi the 0/1 band of half-width r.  The paper cuts Pi into three 16x16
+// fragments per output fragment (out-halo scheme, Sec. IV, Eqs. 4-5, Alg. 1);
+// here one CTA owns a 128 x 128 output tile and both products are single
+// dense tcgen05 MMAs over a haloed 160 x 160 window:
+//
+//   window  X[y'][x'] = state(y0-16+y', x0-16+x') == 1,  y', x' in [0, 160)
+//   band    B[m][k]   = 1 iff k - m in [16-r, 16+r],       m < 128, k < 160
+//   pass 1  D1[x][y'] = sum_x' B[x][x'] X[y'][x']   = H^T   (M=128, N=160, K=160)
+//   pass 2  D2[y][x]  = sum_y' B[y][y'] D1[x][y']   = S     (M=128, N=128, K=160)
+//
+// The window offset is a fixed 16 cells for every r <= 16, so every TMA load
+// starts on a 16-byte boundary; r only changes the band.  Cells outside the
+// grid arrive as TMA zero fill (dead ghost cells, the zero halo of Sec. IV).
+// D1 leaves TMEM lane-locally (lane x owns row x of H^T, which is row x of the
+// K-major pass-2 operand), so no transpose is needed between the passes; D2
+// has one output row per TMEM lane, so the epilogue reads 16 contiguous
+// centre states and writes 16 contiguous next states per access.
+//
+// Roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
+// issuer, warps 2..9 = workers (D1 -> pass-2 operand conversion, encoding
+// of the window when needed, and the fused transition epilogue + TMA store).
+// Every wait is bounded; on timeout the CTA records kDevErrTimeout, drains its
+// own in-flight copies and MMAs, frees TMEM and returns.
+#include <cuda_fp16.h>
+
+#include "cat_internal.h"
+#include "ptx.cuh"
+
+namespace cat {
+namespace tc {
+
+constexpr int kTile = 128;
+constexpr int kWin = 160;
+constexpr int kWorkerWarps = 8;
+constexpr int kThreads = 32 * (2 + kWorkerWarps);
+constexpr int kRegions = 3;
+constexpr int kRegionCols = 160;
+constexpr uint32_t kTmemCols = 512;
+
+// Byte offset of the element at byte position kb (= k * E) of row `row` in a
+// K-major operand tile of R rows.  A row holds 160 elements of E bytes, split
+// into E blocks of 128 bytes (128B swizzle, rows at 128 B pitch) followed by E
+// blocks of 32 bytes (32B swizzle, rows at 32 B pitch).  The swizzles XOR the
+// 16-byte chunk index with address bits [7,10) (128B) or bit 7 (32B).
+__device__ __forceinline__ uint32_t op_off(int R, int E, int row, int kb) {
+  if (kb < 128 * E) {
+    const int blk = kb >> 7, w = kb & 127;
+    return blk * R * 128 + row * 128 + ((((w >> 4) ^ row) & 7) << 4) + (w & 15);
+  }
+  const int kk = kb - 128 * E, blk = kk >> 5, w = kk & 31;
+  return E * R * 128 + blk * R * 32 + row * 32 + ((((w >> 4) ^ (row >> 2)) & 1) << 4) + (w & 15);
+}
+
+// UMMA descriptor of the 32-byte K-step j of such a tile at shared address base.
+__device__ __forceinline__ uint64_t op_desc(uint32_t base, int R, int E, int j) {
+  const int kb = 32 * j;
+  if (kb < 128 * E) return smem_desc(base + (kb >> 7) * R * 128 + (kb & 127), 16, 1024, kSwizzle128B);
+  const int kk = kb - 128 * E;
+  return smem_desc(base + E * R * 128 + (kk >> 5) * R * 32, 16, 256, kSwizzle32B);
+}
+
+template <int E, int NS, bool ENC, int NPLANES>
+struct Layout {
+  static constexpr uint32_t kBand = 0;
+  static constexpr uint32_t kBandBytes = kTile * kWin * E;
+  static constexpr uint32_t kXs = kBand + kBandBytes;     // u8 windows (TMA)
+  static constexpr uint32_t kXsBytes = kWin * kWin;
+  static constexpr uint32_t kXe = kXs + NS * kXsBytes;     // encoded window
+  static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E : 0;
+  static constexpr uint32_t kH = kXe + kXeBytes;           // pass-2 operand planes
+  static constexpr uint32_t kHBytes = kTile * kWin * E;
+  static constexpr uint32_t kOut = kH + NPLANES * kHBytes; // output staging x2
+  static constexpr uint32_t kOutBytes = kTile * kTile;
+  static constexpr uint32_t kBars = kOut + 2 * kOutBytes;
+  static constexpr uint32_t kTotal = kBars + 512;
+  static constexpr uint32_t kDyn = kTotal + 1024;          // + alignment slack
+};
+
+struct Bars {
+  uint64_t x_full[3], x_empty[3];
+  uint64_t d1_full[kRegions], d2_full[kRegions], tmem_empty[kRegions];
+  uint64_t h_full, enc_full;
+  uint64_t out_free[2], out_full[2];
+  uint64_t mma_done, never;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ void set_abort(Bars *b, const TcParams &p, int where) {
+  b->abort = 1;
+  if (p.err) atomicCAS(p.err, 0, kDevErrTimeout | where);
+}
+
+// Every lane waits; the warp agrees on the outcome.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *b,
+                                          const TcParams &p) {
+  bool ok = mbar_wait(bar, parity, &b->abort, p.timeout_ns);
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Encodes the 160 x 160 u8 window xs as operand values (1 -> one, else 0).
+template <int E>
+__device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bool multistate,
+                                              int tid, int nthr) {
+  for (int q = tid; q < kWin * 10; q += nthr) {
+    const int row = q / 10, c = q - row * 10;
+    uint4 v = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, row, 16 * c));
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    if (multistate) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[i] = __vcmpeq4(w[i], 0x01010101u) & 0x01010101u;
+    }
+    if constexpr (E == 1) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[i] *= 0x38u;  // e4m3 1.0
+      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      uint32_t h[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        h[2 * i] = __byte_perm(w[i], 0, 0x4140) * 0x3C00u;      // fp16 1.0 per 0/1 byte
+        h[2 * i + 1] = __byte_perm(w[i], 0, 0x4342) * 0x3C00u;
+      }
+      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 2, row, 32 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 2, row, 32 * c + 16)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Next state of one cell from its box count s and state c (see RuleDev).
+__device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev &R) {
+  if (c == 0) return (uint32_t)(s - R.b_lo) <= (uint32_t)R.b_w;
+  if (c == 1) return ((uint32_t)(s - R.s_lo) <= (uint32_t)R.s_w) ? 1u : (R.C > 2 ? 2u : 0u);
+  return (c + 1 == (uint32_t)R.C) ? 0u : c + 1;
+}
+
+template <int DT, bool ENC>
+__global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
+  constexpr int E = DT == 0 ? 2 : 1;            // operand bytes (FP16 / FP8 e4m3)
+  constexpr int NS = DT == 0 ? 2 : 3;           // TMA window stages
+  constexpr int NPLANES = DT == 0 ? 1 : 2;      // pass-2 operand planes
+  constexpr int KSTEPS = 5 * E;                 // 160 / (32 / E)
+  using L = Layout<E, NS, ENC, NPLANES>;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars *bars = reinterpret_cast<Bars *>(smem + L::kBars);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const RuleDev R = p.rule;
+  const int n_my = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const bool multistate = R.C > 2;
+  const int nplanes = (DT == 1 && 2 * R.r + 1 > 15) ? 2 : 1;   // e4m3 holds 0..16 exactly
+  const float d1_scale = (DT == 1 && !ENC) ? 512.0f : 1.0f;     // raw 0x01 byte = 2^-9
+
+  // ---- set-up: barriers, TMEM, band ------------------------------------
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) { mbar_init(&bars->x_full[i], 1); mbar_init(&bars->x_empty[i], kWorkerWarps); }
+    for (int i = 0; i < kRegions; ++i) {
+      mbar_init(&bars->d1_full[i], 1);
+      mbar_init(&bars->d2_full[i], 1);
+      mbar_init(&bars->tmem_empty[i], kWorkerWarps);
+    }
+    mbar_init(&bars->h_full, kWorkerWarps);
+    mbar_init(&bars->enc_full, kWorkerWarps);
+    for (int i = 0; i < 2; ++i) { mbar_init(&bars->out_free[i], 1); mbar_init(&bars->out_full[i], kWorkerWarps); }
+    mbar_init(&bars->mma_done, 1);
+    mbar_init(&bars->never, 1);
+    bars->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&bars->tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
+  {  // band B[m][k] = one iff k - m in [16 - r, 16 + r]; 128 rows x 10E chunks of 16 bytes
+    uint8_t *band = smem + L::kBand;
+    for (int q = threadIdx.x; q < kTile * 10 * E; q += kThreads) {
+      const int m = q / (10 * E), c = q - m * (10 * E);
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4 / E; ++b) {
+          const int k = (16 * c + 4 * i) / E + b;
+          const int d = k - m;
+          const bool on = d >= 16 - R.r && d <= 16 + R.r;
+          word |= on ? (E == 1 ? (0x38u << (8 * b)) : (0x3C00u << (16 * b))) : 0u;
+        }
+        w[i] = word;
+      }
+      *reinterpret_cast<uint4 *>(band + op_off(kTile, E, m, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  const uint32_t s_base = smem_u32(smem);
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&p.map_in_a);
+      prefetch_tmap(&p.map_in_b);
+      int issued = 0;
+      for (int j = 0; j < n_my; ++j) {
+        const int s = j % NS;
+        if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 1); break; }
+        const int t = blockIdx.x + j * gridDim.x;
+        const int ty = t / p.tiles_x, tx = t - ty * p.tiles_x;
+        uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
+        mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
+        tma_load_2d(xs, &p.map_in_a, tx * kTile - 16, ty * kTile - 16, &bars->x_full[s]);
+        tma_load_2d(xs + kWin * 128, &p.map_in_b, tx * kTile + 112, ty * kTile - 16, &bars->x_full[s]);
+        issued = j + 1;
+      }
+      // drain: the last load issued into each stage must have landed
+      volatile int no_abort = 0;
+      for (int j = issued - 1; j >= 0 && j >= issued - NS; --j)
+        if (!mbar_wait(&bars->x_full[j % NS], (j / NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, p, 2);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc1 = idesc_f32acc(128, kWin);
+      const uint32_t idesc2 = idesc_f32acc(128, kTile);
+      const uint32_t band = s_base + L::kBand;
+      bool ok = true;
+      if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
+        ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
+        if (!ok) set_abort(bars, p, 3);
+      }
+      for (int j = 0; ok && j <= n_my; ++j) {
+        if (j < n_my) {  // pass 1 of tile j
+          const int reg = j % kRegions, s = j % NS;
+          ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns);
+          if (ok) ok = ENC ? mbar_wait(&bars->enc_full, j & 1, &bars->abort, p.timeout_ns)
+                           : mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
+          if (!ok) { set_abort(bars, p, 4); break; }
+          tc_fence_after();
+          const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
+          const uint32_t d1 = tmem + reg * kRegionCols;
+#pragma unroll
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(win, kWin, E, k);
+            if constexpr (DT == 0) mma_f16(d1, a, b, idesc1, k > 0);
+            else mma_f8f6f4(d1, a, b, idesc1, k > 0);
+          }
+          mma_commit(&bars->d1_full[reg]);
+        }
+        if (j >= 1) {  // pass 2 of tile j - 1
+          const int jj = j - 1, reg = jj % kRegions;
+          if (!mbar_wait(&bars->h_full, jj & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 5); ok = false; break; }
+          tc_fence_after();
+          const uint32_t d2 = tmem + reg * kRegionCols;
+          for (int pl = 0; pl < nplanes; ++pl) {
+            const uint32_t hop = s_base + L::kH + pl * L::kHBytes;
+#pragma unroll
+            for (int k = 0; k < KSTEPS; ++k) {
+              const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(hop, kTile, E, k);
+              if constexpr (DT == 0) mma_f16(d2, a, b, idesc2, (pl | k) > 0);
+              else mma_f8f6f4(d2, a, b, idesc2, (pl | k) > 0);
+            }
+          }
+          mma_commit(&bars->d2_full[reg]);
+        }
+      }
+      // drain: every MMA issued above has completed before TMEM is freed
+      mma_commit(&bars->mma_done);
+      volatile int no_abort = 0;
+      if (!mbar_wait(&bars->mma_done, 0, &no_abort, p.timeout_ns)) set_abort(bars, p, 6);
+    }
+  } else {
+    // --------------------------------------------------------------- workers
+    const int wtid = threadIdx.x - 64;            // 0..255
+    const int q = warp & 3;                       // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;             // which half of the columns
+    const int row = 32 * q + lane;                // TMEM lane = x (pass 1) / y (pass 2)
+    const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
+    const bool store_thread = wtid == 0;
+    uint8_t *hop = smem + L::kH;
+    bool ok = true;
+    if (ENC && n_my > 0) {
+      ok = warp_wait(&bars->x_full[0], 0, bars, p);
+      if (ok) {
+        encode_window<E>(smem + L::kXs, smem + L::kXe, multistate, wtid, 32 * kWorkerWarps);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->enc_full);
+      }
+    }
+    for (int j = 0; ok && j < n_my; ++j) {
+      const int reg = j % kRegions, s = j % NS, o = j & 1;
+      const int t = blockIdx.x + j * gridDim.x;
+      const int ty = t / p.tiles_x, tx = t - ty * p.tiles_x;
+      const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
+      const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
+
+      // ---- D1 (H^T) -> pass-2 operand
+      if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p))) break;
+      tc_fence_after();
+      {
+        uint32_t v[5][16];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tmem_ld16(treg + 16 * (5 * half + c), v[c]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const int cc = 5 * half + c;  // columns y' = 16cc .. 16cc+15
+          if constexpr (E == 2) {
+            uint32_t h[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              __half2 hv = __floats2half2_rn(__uint_as_float(v[c][2 * i]), __uint_as_float(v[c][2 * i + 1]));
+              h[i] = *reinterpret_cast<uint32_t *>(&hv);
+            }
+            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc + 16)) = make_uint4(h[4], h[5], h[6], h[7]);
+          } else {
+            uint32_t lo[4], hi[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float f[4], fl[4], fh[4];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                f[b] = __uint_as_float(v[c][4 * i + b]) * d1_scale;
+                fh[b] = nplanes == 2 ? floorf(f[b] * 0.0625f) * 16.0f : 0.0f;  // 0, 16 or 32
+                fl[b] = f[b] - fh[b];                                          // 0..15
+              }
+              lo[i] = e4m3x2(fl[0], fl[1]) | (e4m3x2(fl[2], fl[3]) << 16);
+              hi[i] = e4m3x2(fh[0], fh[1]) | (e4m3x2(fh[2], fh[3]) << 16);
+            }
+            const uint32_t off = op_off(kTile, 1, row, 16 * cc);
+            *reinterpret_cast<uint4 *>(hop + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            if (nplanes == 2)
+              *reinterpret_cast<uint4 *>(hop + L::kHBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->h_full);
+
+      // ---- encode the next window while pass 2 runs
+      if (ENC && j + 1 < n_my) {
+        const int s1 = (j + 1) % NS;
+        if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p))) break;
+        encode_window<E>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, multistate, wtid, 32 * kWorkerWarps);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->enc_full);
+      }
+
+      // ---- epilogue: S -> next state, staged for the TMA store
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p))) break;
+      tc_fence_after();
+      if (store_thread) {
+        bulk_wait_read<1>();  // the store that last read out[o] (tile j-2) is done
+        mbar_arrive(&bars->out_free[o]);
+      }
+      if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p))) break;
+      uint8_t *out = smem + L::kOut + o * L::kOutBytes;
+      {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld16(treg + 16 * (4 * half + c), v[c]);
+        tmem_wait_ld();
+        const int y = row;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int cc = 4 * half + c;  // x = 16cc .. 16cc+15
+          const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
+          const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
+          if (p.sums) {
+            const int gy = ty * kTile + y;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int gx = tx * kTile + 16 * cc + i;
+              if (gy < p.H && gx < p.W)
+                p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]));
+            }
+          } else {
+            uint32_t ow[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              uint32_t word = 0;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                const int s_cnt = __float2int_rn(__uint_as_float(v[c][4 * i + b]));
+                const uint32_t st = (cw[i] >> (8 * b)) & 0xFFu;
+                uint32_t nx;
+                if (!multistate) {
+                  const int lo = st ? R.s_lo : R.b_lo;
+                  const int wd = st ? R.s_w : R.b_w;
+                  nx = (uint32_t)(s_cnt - lo) <= (uint32_t)wd;
+                } else {
+                  nx = next_state(s_cnt, st, R);
+                }
+                word |= nx << (8 * b);
+              }
+              ow[i] = word;
+            }
+            *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars->out_full[o]);
+        mbar_arrive(&bars->tmem_empty[reg]);
+        mbar_arrive(&bars->x_empty[s]);
+      }
+      if (store_thread) {
+        if (!mbar_wait(&bars->out_full[o], (j >> 1) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 7); ok = false; }
+        else if (!p.sums) {
+          tma_store_2d(&p.map_out, tx * kTile, ty * kTile, out);
+        }
+        bulk_commit();
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    }
+    if (!ok) set_abort(bars, p, 8);
+    if (store_thread) bulk_wait<0>();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace tc
+
+size_t tc_smem_bytes(int dt, bool encode) {
+  if (dt == 1) return tc::Layout<2, 2, true, 1>::kDyn;
+  return encode ? tc::Layout<1, 3, true, 2>::kDyn : tc::Layout<1, 3, false, 2>::kDyn;
+}
+
+template <int DT, bool ENC>
+static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, size_t smem) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  tc::ltl_tc_kernel<DT, ENC><<<grid, tc::kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
+  if (dt == 1) return launch_one<0, true>(p, grid, s, tc_smem_bytes(1, true));
+  if (encode) return launch_one<1, true>(p, grid, s, tc_smem_bytes(2, true));
+  return launch_one<1, false>(p, grid, s, tc_smem_bytes(2, false));
+}
+
+}  // namespace cat
