@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--size", type=int, default=N)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparator kernels")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="side of the oracle's sample window")
+    ap.add_argument("--radii", default="1-16", help="radii to run, e.g. 1-16 or 16 or 1,8,16")
     return ap.parse_args()
 
 
@@ -318,8 +319,22 @@ def run_cat(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def parse_radii(spec: str):
+    out = []
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            out += list(range(int(a), int(b) + 1))
+        else:
+            out.append(int(part))
+    assert all(1 <= r <= 16 for r in out)
+    return out
+
+
 def main():
+    global RADII
     args = parse()
+    RADII = parse_radii(args.radii)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
