@@ -4,6 +4,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -181,6 +182,124 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
   return CAT_OK;
 }
 
+// ---------------------------------------------------------------- batches
+// A batch plan: the per-instance descriptor table and the tile work-list of
+// one handle list, kept on the device, plus cached CUDA graphs of n launches.
+struct BatchPlan {
+  std::vector<cat_instance *> hs;
+  std::vector<int> cur0;      // each instance's current buffer when the table was built
+  int64_t steps_done = 0;     // steps advanced through this plan since then
+  int32_t dtype = 0;
+  bool encode = false;
+  cat::BatchInst *d_inst = nullptr;
+  cat::BatchTile *d_tiles = nullptr;
+  int n_tiles = 0, grid = 0;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // by start parity
+  int64_t exec_steps[2] = {0, 0};
+  cudaStream_t capture_stream = nullptr;
+};
+
+std::mutex g_plan_mu;
+std::vector<BatchPlan *> g_plans;
+
+void free_plan(BatchPlan *pl) {
+  for (int i = 0; i < 2; ++i)
+    if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
+  if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
+  cudaFree(pl->d_inst);
+  cudaFree(pl->d_tiles);
+  delete pl;
+}
+
+void drop_plans_with(cat_instance *h) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    if (std::find((*it)->hs.begin(), (*it)->hs.end(), h) != (*it)->hs.end()) {
+      free_plan(*it);
+      it = g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// (Re)writes the instance table of a plan from the handles' current state.
+int upload_instances(BatchPlan *pl) {
+  CAT_CUDA(cudaDeviceSynchronize());  // earlier launches of this plan may still read the table
+  std::vector<cat::BatchInst> inst(pl->hs.size());
+  memset(inst.data(), 0, inst.size() * sizeof(cat::BatchInst));
+  pl->cur0.resize(pl->hs.size());
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    const cat_instance *h = pl->hs[i];
+    for (int b = 0; b < 2; ++b) {
+      inst[i].map_in_a[b] = h->maps[b][0];
+      inst[i].map_in_b[b] = h->maps[b][1];
+      inst[i].map_out[b] = h->maps[b][2];
+    }
+    inst[i].rule = h->rd;
+    inst[i].H = (int32_t)h->H;
+    inst[i].W = (int32_t)h->W;
+    inst[i].cur = h->cur;
+    inst[i].err = h->d_err;
+    pl->cur0[i] = h->cur;
+  }
+  CAT_CUDA(cudaMemcpy(pl->d_inst, inst.data(), inst.size() * sizeof(cat::BatchInst), cudaMemcpyHostToDevice));
+  pl->steps_done = 0;
+  for (int i = 0; i < 2; ++i) {
+    if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
+    pl->exec[i] = nullptr;
+    pl->exec_steps[i] = 0;
+  }
+  return CAT_OK;
+}
+
+int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
+  BatchPlan *pl = new (std::nothrow) BatchPlan();
+  if (!pl) return fail(CAT_ERR_OOM, "host allocation failed");
+  pl->hs.assign(hs, hs + count);
+  pl->dtype = hs[0]->dtype;
+  pl->encode = false;
+  for (int32_t i = 0; i < count; ++i) pl->encode |= hs[i]->rule.C > 2;
+  // work-list: instances ordered by radius, tiles row-major within an instance
+  std::vector<int> order(count);
+  for (int32_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->rule.r < hs[b]->rule.r; });
+  std::vector<cat::BatchTile> tiles;
+  for (int i : order) {
+    const int64_t ty = (hs[i]->H + 127) / 128, tx = (hs[i]->W + 127) / 128;
+    for (int64_t y = 0; y < ty; ++y)
+      for (int64_t x = 0; x < tx; ++x) tiles.push_back(cat::BatchTile{i, (int16_t)y, (int16_t)x});
+  }
+  if (tiles.size() > (size_t)INT32_MAX) { delete pl; return fail(CAT_ERR_UNSUPPORTED, "batch too large"); }
+  pl->n_tiles = (int)tiles.size();
+  pl->grid = std::min(pl->n_tiles, hs[0]->dev.sms);
+  cudaError_t e = cudaMalloc(&pl->d_inst, sizeof(cat::BatchInst) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tiles, sizeof(cat::BatchTile) * tiles.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_tiles, tiles.data(), sizeof(cat::BatchTile) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "batch plan"); }
+  int rc = upload_instances(pl);
+  if (rc) { free_plan(pl); return rc; }
+  *out = pl;
+  return CAT_OK;
+}
+
+int launch_batch_steps(BatchPlan *pl, int64_t n_steps, int64_t start, cudaStream_t s) {
+  cat::TcParams p;
+  memset(&p, 0, sizeof(p));
+  p.n_tiles = pl->n_tiles;
+  p.timeout_ns = pl->hs[0]->timeout_ns;
+  p.binst = pl->d_inst;
+  p.btiles = pl->d_tiles;
+  for (int64_t t = 0; t < n_steps; ++t) {
+    p.parity = (int32_t)((start + t) & 1);
+    cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pl->encode, pl->grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  }
+  return CAT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -287,14 +406,69 @@ int cat_step(cat_handle_t h, int64_t n_steps, void *stream) {
 
 int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream) {
   if (!hs || count < 0 || n_steps < 0) return fail(CAT_ERR_INVALID_ARG, "bad batch arguments");
-  for (int32_t i = 0; i < count; ++i)
+  for (int32_t i = 0; i < count; ++i) {
     if (!hs[i]) return fail(CAT_ERR_INVALID_ARG, "instance %d is NULL", i);
-  for (int64_t t = 0; t < n_steps; ++t)
-    for (int32_t i = 0; i < count; ++i) {
-      int rc = launch_step(hs[i], hs[i]->cur, nullptr, 0, (cudaStream_t)stream);
-      if (rc) return rc;
-      hs[i]->cur ^= 1;
+    for (int32_t k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) return fail(CAT_ERR_INVALID_ARG, "instance %d appears twice", i);
+  }
+  if (count == 0 || n_steps == 0) return CAT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool all_tc = true;
+  for (int32_t i = 0; i < count; ++i) {
+    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05;
+    if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
+      return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
+    if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)
+      return fail(CAT_ERR_UNSUPPORTED, "batched instances are limited to 4194176 x 4194176 cells");
+  }
+  if (!all_tc) {  // the comparator kernels have no batched launch: one launch per instance and step
+    for (int64_t t = 0; t < n_steps; ++t)
+      for (int32_t i = 0; i < count; ++i) {
+        int rc = launch_step(hs[i], hs[i]->cur, nullptr, 0, s);
+        if (rc) return rc;
+        hs[i]->cur ^= 1;
+      }
+    return CAT_OK;
+  }
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  BatchPlan *pl = nullptr;
+  for (BatchPlan *c : g_plans)
+    if ((int32_t)c->hs.size() == count && std::equal(c->hs.begin(), c->hs.end(), hs) && c->dtype == hs[0]->dtype) {
+      pl = c;
+      break;
     }
+  int rc;
+  if (!pl) {
+    if ((rc = build_plan(hs, count, &pl))) return rc;
+    g_plans.push_back(pl);
+  }
+  bool in_sync = true;
+  for (int32_t i = 0; i < count; ++i) in_sync &= hs[i]->cur == (pl->cur0[i] ^ (int)(pl->steps_done & 1));
+  if (!in_sync && (rc = upload_instances(pl))) return rc;
+  const int par = (int)(pl->steps_done & 1);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CAT_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    if ((rc = launch_batch_steps(pl, n_steps, pl->steps_done, s))) return rc;
+  } else {
+    if (!pl->exec[par] || pl->exec_steps[par] != n_steps) {
+      if (pl->exec[par]) cudaGraphExecDestroy(pl->exec[par]);
+      pl->exec[par] = nullptr;
+      cudaGraph_t g = nullptr;
+      CAT_CUDA(cudaStreamBeginCapture(pl->capture_stream, cudaStreamCaptureModeThreadLocal));
+      rc = launch_batch_steps(pl, n_steps, pl->steps_done, pl->capture_stream);
+      cudaError_t e = cudaStreamEndCapture(pl->capture_stream, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&pl->exec[par], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      pl->exec_steps[par] = n_steps;
+    }
+    CAT_CUDA(cudaGraphLaunch(pl->exec[par], s));
+  }
+  pl->steps_done += n_steps;
+  for (int32_t i = 0; i < count; ++i) hs[i]->cur ^= (int)(n_steps & 1);
   return CAT_OK;
 }
 
@@ -331,6 +505,7 @@ int cat_debug_control(cat_handle_t h, int32_t what, int64_t value) {
 int cat_destroy(cat_handle_t h) {
   if (!h) return CAT_OK;
   cudaDeviceSynchronize();
+  drop_plans_with(h);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_err);

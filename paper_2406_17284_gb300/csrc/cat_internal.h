@@ -18,8 +18,28 @@ struct RuleDev {
   int32_t pad;
 };
 
-// Parameters of the tcgen05 step kernel (one instance; passed as a
-// __grid_constant__ so the tensor maps live in parameter space).
+// One instance of a batched launch (global memory, read by the kernel).
+// Buffer b of the instance is read through map_in_a[b] / map_in_b[b] and
+// written through map_out[b]; the state of step t lives in buffer cur ^ (t & 1).
+struct BatchInst {
+  CUtensorMap map_in_a[2];
+  CUtensorMap map_in_b[2];
+  CUtensorMap map_out[2];
+  RuleDev rule;
+  int32_t H, W, cur, pad;
+  int32_t *err;
+};
+
+// One 128 x 128 output tile of a batched launch.
+struct BatchTile {
+  int32_t inst;
+  int16_t ty, tx;
+};
+
+// Parameters of the tcgen05 step kernel (passed as a __grid_constant__ so the
+// tensor maps of a single instance live in parameter space).  In batch mode
+// the tiles come from `btiles` (each CTA takes a contiguous chunk) and the
+// per-instance maps and rules from `binst`; the single-instance fields are unused.
 struct TcParams {
   CUtensorMap map_in_a;  // input buffer, box 128 x 160 bytes, 128B swizzle
   CUtensorMap map_in_b;  // input buffer, box  32 x 160 bytes,  32B swizzle
@@ -31,7 +51,9 @@ struct TcParams {
   int64_t sums_ld;  // row stride of sums (elements)
   uint64_t timeout_ns;
   int32_t inject;   // 1: wait on a barrier nobody arrives at (timeout test)
-  int32_t pad0;
+  int32_t parity;   // batch mode: step index & 1
+  const BatchInst *binst;
+  const BatchTile *btiles;
 };
 
 // Parameters of the warp-level kernels (mma.sync fragments, CUDA-core stencil).
@@ -51,6 +73,7 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 // encode: FP8 only -- stage the operand through an encoded copy of the window
 // (needed when C > 2; otherwise the raw 0/1 bytes are used as e4m3 operands).
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
+cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
 size_t tc_smem_bytes(int dt, bool encode);
 
 // Paper-style fragment kernels (cat_mma.cu).  dt: FP16 or INT8.

@@ -83,22 +83,21 @@ struct Layout {
 struct Bars {
   uint64_t x_full[3], x_empty[3];
   uint64_t d1_full[kRegions], d2_full[kRegions], tmem_empty[kRegions];
-  uint64_t h_full, enc_full;
+  uint64_t h_full, enc_full, band_ready;
   uint64_t out_free[2], out_full[2];
   uint64_t mma_done, never;
   uint32_t tmem_base;
   int abort;
 };
 
-__device__ __forceinline__ void set_abort(Bars *b, const TcParams &p, int where) {
+__device__ __forceinline__ void set_abort(Bars *b, int32_t *err, int where) {
   b->abort = 1;
-  if (p.err) atomicCAS(p.err, 0, kDevErrTimeout | where);
+  if (err) atomicCAS(err, 0, kDevErrTimeout | where);
 }
 
 // Every lane waits; the warp agrees on the outcome.
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *b,
-                                          const TcParams &p) {
-  bool ok = mbar_wait(bar, parity, &b->abort, p.timeout_ns);
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *b, uint64_t timeout_ns) {
+  bool ok = mbar_wait(bar, parity, &b->abort, timeout_ns);
   return __all_sync(0xffffffffu, ok);
 }
 
@@ -131,6 +130,28 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
   }
 }
 
+// Band B[m][k] = one iff k - m in [16 - r, 16 + r]; 128 rows x 10E chunks of 16 bytes.
+template <int E>
+__device__ __forceinline__ void build_band(uint8_t *band, int r, int tid, int nthr) {
+  for (int q = tid; q < kTile * 10 * E; q += nthr) {
+    const int m = q / (10 * E), c = q - m * (10 * E);
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int b = 0; b < 4 / E; ++b) {
+        const int k = (16 * c + 4 * i) / E + b;
+        const int d = k - m;
+        const bool on = d >= 16 - r && d <= 16 + r;
+        word |= on ? (E == 1 ? (0x38u << (8 * b)) : (0x3C00u << (16 * b))) : 0u;
+      }
+      w[i] = word;
+    }
+    *reinterpret_cast<uint4 *>(band + op_off(kTile, E, m, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 __device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
   uint16_t r;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
@@ -144,7 +165,64 @@ __device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev 
   return (c + 1 == (uint32_t)R.C) ? 0u : c + 1;
 }
 
-template <int DT, bool ENC>
+// What one output tile needs: its maps, origin, grid extent and rule.
+struct Tile {
+  const CUtensorMap *in_a, *in_b, *out;
+  int x0, y0, H, W;
+  RuleDev R;
+  int32_t *err;
+};
+
+// Tiles of this CTA: single instance -> t = blockIdx + j * gridDim (row-major
+// waves, so halo rows are L2 hits); batch -> a contiguous chunk of the
+// work-list (sorted by radius, so the band rarely changes).
+template <bool BATCH>
+__device__ __forceinline__ void my_range(const TcParams &p, int &first, int &count) {
+  if constexpr (BATCH) {
+    const int64_t n = p.n_tiles, g = gridDim.x, b = blockIdx.x;
+    first = (int)(b * n / g);
+    count = (int)((b + 1) * n / g) - first;
+  } else {
+    first = 0;
+    count = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  }
+}
+
+template <bool BATCH>
+__device__ __forceinline__ Tile get_tile(const TcParams &p, int first, int j) {
+  Tile t;
+  if constexpr (BATCH) {
+    const BatchTile bt = p.btiles[first + j];
+    const BatchInst *I = p.binst + bt.inst;
+    const int in = I->cur ^ p.parity;
+    t.in_a = &I->map_in_a[in];
+    t.in_b = &I->map_in_b[in];
+    t.out = &I->map_out[in ^ 1];
+    t.x0 = bt.tx * kTile;
+    t.y0 = bt.ty * kTile;
+    t.H = I->H;
+    t.W = I->W;
+    t.R = I->rule;
+    t.err = I->err;
+  } else {
+    const int id = (int)blockIdx.x + j * (int)gridDim.x;
+    const int ty = id / p.tiles_x, tx = id - ty * p.tiles_x;
+    t.in_a = &p.map_in_a;
+    t.in_b = &p.map_in_b;
+    t.out = &p.map_out;
+    t.x0 = tx * kTile;
+    t.y0 = ty * kTile;
+    t.H = p.H;
+    t.W = p.W;
+    t.R = p.rule;
+    t.err = p.err;
+  }
+  return t;
+}
+
+__device__ __forceinline__ int planes_for(int DT, int r) { return (DT == 1 && 2 * r + 1 > 15) ? 2 : 1; }
+
+template <int DT, bool ENC, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
   constexpr int E = DT == 0 ? 2 : 1;            // operand bytes (FP16 / FP8 e4m3)
   constexpr int NS = DT == 0 ? 2 : 3;           // TMA window stages
@@ -156,11 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Bars *bars = reinterpret_cast<Bars *>(smem + L::kBars);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const RuleDev R = p.rule;
-  const int n_my = (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const bool multistate = R.C > 2;
-  const int nplanes = (DT == 1 && 2 * R.r + 1 > 15) ? 2 : 1;   // e4m3 holds 0..16 exactly
-  const float d1_scale = (DT == 1 && !ENC) ? 512.0f : 1.0f;     // raw 0x01 byte = 2^-9
+  int first, n_my;
+  my_range<BATCH>(p, first, n_my);
+  const float d1_scale = (DT == 1 && !ENC) ? 512.0f : 1.0f;     // raw 0x01 byte = e4m3 2^-9
+  int32_t *err0 = BATCH ? (n_my > 0 ? get_tile<BATCH>(p, first, 0).err : nullptr) : p.err;
+  const int r0 = n_my > 0 ? get_tile<BATCH>(p, first, 0).R.r : 1;
 
   // ---- set-up: barriers, TMEM, band ------------------------------------
   if (threadIdx.x == 0) {
@@ -172,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     mbar_init(&bars->h_full, kWorkerWarps);
     mbar_init(&bars->enc_full, kWorkerWarps);
+    mbar_init(&bars->band_ready, kWorkerWarps);
     for (int i = 0; i < 2; ++i) { mbar_init(&bars->out_free[i], 1); mbar_init(&bars->out_full[i], kWorkerWarps); }
     mbar_init(&bars->mma_done, 1);
     mbar_init(&bars->never, 1);
@@ -182,26 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     tmem_alloc(&bars->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  {  // band B[m][k] = one iff k - m in [16 - r, 16 + r]; 128 rows x 10E chunks of 16 bytes
-    uint8_t *band = smem + L::kBand;
-    for (int q = threadIdx.x; q < kTile * 10 * E; q += kThreads) {
-      const int m = q / (10 * E), c = q - m * (10 * E);
-      uint32_t w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int b = 0; b < 4 / E; ++b) {
-          const int k = (16 * c + 4 * i) / E + b;
-          const int d = k - m;
-          const bool on = d >= 16 - R.r && d <= 16 + R.r;
-          word |= on ? (E == 1 ? (0x38u << (8 * b)) : (0x3C00u << (16 * b))) : 0u;
-        }
-        w[i] = word;
-      }
-      *reinterpret_cast<uint4 *>(band + op_off(kTile, E, m, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-  }
+  build_band<E>(smem + L::kBand, r0, threadIdx.x, kThreads);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -212,24 +272,22 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   if (warp == 0) {
     // ---------------------------------------------------------- TMA producer
     if (lane == 0) {
-      prefetch_tmap(&p.map_in_a);
-      prefetch_tmap(&p.map_in_b);
       int issued = 0;
       for (int j = 0; j < n_my; ++j) {
         const int s = j % NS;
-        if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 1); break; }
-        const int t = blockIdx.x + j * gridDim.x;
-        const int ty = t / p.tiles_x, tx = t - ty * p.tiles_x;
+        const Tile t = get_tile<BATCH>(p, first, j);
+        if (j == 0 || BATCH) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
+        if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
-        tma_load_2d(xs, &p.map_in_a, tx * kTile - 16, ty * kTile - 16, &bars->x_full[s]);
-        tma_load_2d(xs + kWin * 128, &p.map_in_b, tx * kTile + 112, ty * kTile - 16, &bars->x_full[s]);
+        tma_load_2d(xs, t.in_a, t.x0 - 16, t.y0 - 16, &bars->x_full[s]);
+        tma_load_2d(xs + kWin * 128, t.in_b, t.x0 + 112, t.y0 - 16, &bars->x_full[s]);
         issued = j + 1;
       }
       // drain: the last load issued into each stage must have landed
       volatile int no_abort = 0;
       for (int j = issued - 1; j >= 0 && j >= issued - NS; --j)
-        if (!mbar_wait(&bars->x_full[j % NS], (j / NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, p, 2);
+        if (!mbar_wait(&bars->x_full[j % NS], (j / NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 2);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -238,17 +296,49 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const uint32_t idesc2 = idesc_f32acc(128, kTile);
       const uint32_t band = s_base + L::kBand;
       bool ok = true;
+      int band_r = r0, prev_r = r0, rebuilds = 0;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
         ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
-        if (!ok) set_abort(bars, p, 3);
+        if (!ok) set_abort(bars, err0, 3);
       }
+      auto pass2 = [&](int jj, int r) -> bool {
+        const int reg = jj % kRegions;
+        if (!mbar_wait(&bars->h_full, jj & 1, &bars->abort, p.timeout_ns)) return false;
+        tc_fence_after();
+        const uint32_t d2 = tmem + reg * kRegionCols;
+        const int nplanes = planes_for(DT, r);
+        for (int pl = 0; pl < nplanes; ++pl) {
+          const uint32_t hop = s_base + L::kH + pl * L::kHBytes;
+#pragma unroll
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(hop, kTile, E, k);
+            if constexpr (DT == 0) mma_f16(d2, a, b, idesc2, (pl | k) > 0);
+            else mma_f8f6f4(d2, a, b, idesc2, (pl | k) > 0);
+          }
+        }
+        mma_commit(&bars->d2_full[reg]);
+        return true;
+      };
       for (int j = 0; ok && j <= n_my; ++j) {
+        bool p2_done = false;
+        int rj = prev_r;
+        if (j < n_my) rj = get_tile<BATCH>(p, first, j).R.r;
+        if (BATCH && j < n_my && rj != band_r) {
+          // the band changes: finish tile j-1 on the old band, wait for the new one
+          if (j >= 1) {
+            if (!(ok = pass2(j - 1, prev_r))) { set_abort(bars, err0, 5); break; }
+            p2_done = true;
+          }
+          if (!(ok = mbar_wait(&bars->band_ready, rebuilds & 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 9); break; }
+          ++rebuilds;
+          band_r = rj;
+        }
         if (j < n_my) {  // pass 1 of tile j
           const int reg = j % kRegions, s = j % NS;
           ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns);
           if (ok) ok = ENC ? mbar_wait(&bars->enc_full, j & 1, &bars->abort, p.timeout_ns)
                            : mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
-          if (!ok) { set_abort(bars, p, 4); break; }
+          if (!ok) { set_abort(bars, err0, 4); break; }
           tc_fence_after();
           const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
           const uint32_t d1 = tmem + reg * kRegionCols;
@@ -260,27 +350,15 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           }
           mma_commit(&bars->d1_full[reg]);
         }
-        if (j >= 1) {  // pass 2 of tile j - 1
-          const int jj = j - 1, reg = jj % kRegions;
-          if (!mbar_wait(&bars->h_full, jj & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 5); ok = false; break; }
-          tc_fence_after();
-          const uint32_t d2 = tmem + reg * kRegionCols;
-          for (int pl = 0; pl < nplanes; ++pl) {
-            const uint32_t hop = s_base + L::kH + pl * L::kHBytes;
-#pragma unroll
-            for (int k = 0; k < KSTEPS; ++k) {
-              const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(hop, kTile, E, k);
-              if constexpr (DT == 0) mma_f16(d2, a, b, idesc2, (pl | k) > 0);
-              else mma_f8f6f4(d2, a, b, idesc2, (pl | k) > 0);
-            }
-          }
-          mma_commit(&bars->d2_full[reg]);
+        if (j >= 1 && !p2_done) {  // pass 2 of tile j - 1
+          if (!(ok = pass2(j - 1, prev_r))) { set_abort(bars, err0, 5); break; }
         }
+        prev_r = rj;
       }
       // drain: every MMA issued above has completed before TMEM is freed
       mma_commit(&bars->mma_done);
       volatile int no_abort = 0;
-      if (!mbar_wait(&bars->mma_done, 0, &no_abort, p.timeout_ns)) set_abort(bars, p, 6);
+      if (!mbar_wait(&bars->mma_done, 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 6);
     }
   } else {
     // --------------------------------------------------------------- workers
@@ -292,10 +370,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     const bool store_thread = wtid == 0;
     uint8_t *hop = smem + L::kH;
     bool ok = true;
+    int band_r = r0;
     if (ENC && n_my > 0) {
-      ok = warp_wait(&bars->x_full[0], 0, bars, p);
+      const Tile t0 = get_tile<BATCH>(p, first, 0);
+      ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
       if (ok) {
-        encode_window<E>(smem + L::kXs, smem + L::kXe, multistate, wtid, 32 * kWorkerWarps);
+        encode_window<E>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, 32 * kWorkerWarps);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
@@ -303,13 +383,23 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     for (int j = 0; ok && j < n_my; ++j) {
       const int reg = j % kRegions, s = j % NS, o = j & 1;
-      const int t = blockIdx.x + j * gridDim.x;
-      const int ty = t / p.tiles_x, tx = t - ty * p.tiles_x;
+      const Tile t = get_tile<BATCH>(p, first, j);
+      const RuleDev &R = t.R;
       const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
       const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
+      const int nplanes = planes_for(DT, R.r);
+
+      // ---- new radius: every MMA on the old band has completed (EPI of j-1 saw it)
+      if (BATCH && R.r != band_r) {
+        build_band<E>(smem + L::kBand, R.r, wtid, 32 * kWorkerWarps);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->band_ready);
+        band_r = R.r;
+      }
 
       // ---- D1 (H^T) -> pass-2 operand
-      if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p))) break;
+      if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       {
         uint32_t v[5][16];
@@ -357,22 +447,24 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       // ---- encode the next window while pass 2 runs
       if (ENC && j + 1 < n_my) {
         const int s1 = (j + 1) % NS;
-        if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p))) break;
-        encode_window<E>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, multistate, wtid, 32 * kWorkerWarps);
+        const bool ms1 = get_tile<BATCH>(p, first, j + 1).R.C > 2;
+        if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
+        encode_window<E>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, 32 * kWorkerWarps);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
       }
 
       // ---- epilogue: S -> next state, staged for the TMA store
-      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p))) break;
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       if (store_thread) {
         bulk_wait_read<1>();  // the store that last read out[o] (tile j-2) is done
         mbar_arrive(&bars->out_free[o]);
       }
-      if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p))) break;
+      if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p.timeout_ns))) break;
       uint8_t *out = smem + L::kOut + o * L::kOutBytes;
+      const bool multistate = R.C > 2;
       {
         uint32_t v[4][16];
 #pragma unroll
@@ -384,12 +476,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           const int cc = 4 * half + c;  // x = 16cc .. 16cc+15
           const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
           const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
-          if (p.sums) {
-            const int gy = ty * kTile + y;
+          if (!BATCH && p.sums) {
+            const int gy = t.y0 + y;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const int gx = tx * kTile + 16 * cc + i;
-              if (gy < p.H && gx < p.W)
+              const int gx = t.x0 + 16 * cc + i;
+              if (gy < t.H && gx < t.W)
                 p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]));
             }
           } else {
@@ -426,15 +518,15 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         mbar_arrive(&bars->x_empty[s]);
       }
       if (store_thread) {
-        if (!mbar_wait(&bars->out_full[o], (j >> 1) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, p, 7); ok = false; }
-        else if (!p.sums) {
-          tma_store_2d(&p.map_out, tx * kTile, ty * kTile, out);
+        if (!mbar_wait(&bars->out_full[o], (j >> 1) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); ok = false; }
+        else if (BATCH || !p.sums) {
+          tma_store_2d(t.out, t.x0, t.y0, out);
         }
         bulk_commit();
       }
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     }
-    if (!ok) set_abort(bars, p, 8);
+    if (!ok) set_abort(bars, err0, 8);
     if (store_thread) bulk_wait<0>();
   }
 
@@ -453,24 +545,30 @@ size_t tc_smem_bytes(int dt, bool encode) {
   return encode ? tc::Layout<1, 3, true, 2>::kDyn : tc::Layout<1, 3, false, 2>::kDyn;
 }
 
-template <int DT, bool ENC>
+template <int DT, bool ENC, bool BATCH>
 static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, size_t smem) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC>,
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_tc_kernel<DT, ENC><<<grid, tc::kThreads, smem, s>>>(p);
+  tc::ltl_tc_kernel<DT, ENC, BATCH><<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 // dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
-  if (dt == 1) return launch_one<0, true>(p, grid, s, tc_smem_bytes(1, true));
-  if (encode) return launch_one<1, true>(p, grid, s, tc_smem_bytes(2, true));
-  return launch_one<1, false>(p, grid, s, tc_smem_bytes(2, false));
+  if (dt == 1) return launch_one<0, true, false>(p, grid, s, tc_smem_bytes(1, true));
+  if (encode) return launch_one<1, true, false>(p, grid, s, tc_smem_bytes(2, true));
+  return launch_one<1, false, false>(p, grid, s, tc_smem_bytes(2, false));
+}
+
+cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
+  if (dt == 1) return launch_one<0, true, true>(p, grid, s, tc_smem_bytes(1, true));
+  if (encode) return launch_one<1, true, true>(p, grid, s, tc_smem_bytes(2, true));
+  return launch_one<1, false, true>(p, grid, s, tc_smem_bytes(2, false));
 }
 
 }  // namespace cat
