@@ -20,11 +20,22 @@
 // has one output row per TMEM lane, so the epilogue reads 16 contiguous
 // centre states and writes 16 contiguous next states per access.
 //
-// Roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
-// issuer, warps 2..9 = workers (D1 -> pass-2 operand conversion, encoding
-// of the window when needed, and the fused transition epilogue + TMA store).
-// Every wait is bounded; on timeout the CTA records kDevErrTimeout, drains its
-// own in-flight copies and MMAs, frees TMEM and returns.
+// Precision (exact in every case, Sec. V-A):
+//   FP16 kernel: X, band and H in f16; D1 = H, D2 = S in f32.
+//   FP8 kernel:  pass 1 on e4m3 -- the raw 0/1 state bytes ARE the B operand
+//                (0x01 reads as e4m3 2^-9), so D1 = H * 2^-9 exactly; pass 2
+//                takes H * 2^-9 as e4m3 when 2r+1 <= 15 (all such values are
+//                e4m3 numbers) and as f16 otherwise (e4m3 cannot hold the odd
+//                counts above 16); D2 = S * 2^-9 in f32.
+// The epilogue compares S (as f16, exact up to 2048) against the rule's
+// ranges two cells at a time in half2 arithmetic.
+//
+// Roles (576 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
+// issuer, warps 2..17 = workers (four per TMEM lane quarter): D1 -> pass-2
+// operand, window encoding when needed, and the fused transition epilogue with
+// the TMA store.  Every wait is bounded; on timeout the CTA records
+// kDevErrTimeout, drains its own in-flight copies and MMAs, frees TMEM and
+// returns.
 #include <cuda_fp16.h>
 
 #include "cat_internal.h"
@@ -35,8 +46,9 @@ namespace tc {
 
 constexpr int kTile = 128;
 constexpr int kWin = 160;
-constexpr int kWorkerWarps = 8;
-constexpr int kThreads = 32 * (2 + kWorkerWarps);
+constexpr int kWorkerWarps = 16;
+constexpr int kWorkerThreads = 32 * kWorkerWarps;
+constexpr int kThreads = 64 + kWorkerThreads;
 constexpr int kRegions = 3;
 constexpr int kRegionCols = 160;
 constexpr uint32_t kTmemCols = 512;
@@ -63,21 +75,26 @@ __device__ __forceinline__ uint64_t op_desc(uint32_t base, int R, int E, int j) 
   return smem_desc(base + E * R * 128 + (kk >> 5) * R * 32, 16, 256, kSwizzle32B);
 }
 
-template <int E, int NS, bool ENC, int NPLANES>
+// DT 0: FP16 kernel; DT 1: FP8 kernel.  ENC: the window is re-encoded in
+// shared memory (always for FP16; for FP8 only when C > 2).
+template <int DT, bool ENC>
 struct Layout {
-  static constexpr uint32_t kBand = 0;
-  static constexpr uint32_t kBandBytes = kTile * kWin * E;
-  static constexpr uint32_t kXs = kBand + kBandBytes;     // u8 windows (TMA)
+  static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
+  static constexpr int NS = (DT == 0 || ENC) ? 2 : 3;         // TMA window stages
+  static constexpr uint32_t kBand16 = 0;                      // f16 band
+  static constexpr uint32_t kBand16Bytes = kTile * kWin * 2;
+  static constexpr uint32_t kBand8 = kBand16 + kBand16Bytes;  // e4m3 band (FP8)
+  static constexpr uint32_t kBand8Bytes = DT == 1 ? kTile * kWin : 0;
+  static constexpr uint32_t kXs = kBand8 + kBand8Bytes;       // u8 windows (TMA)
   static constexpr uint32_t kXsBytes = kWin * kWin;
-  static constexpr uint32_t kXe = kXs + NS * kXsBytes;     // encoded window
-  static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E : 0;
-  static constexpr uint32_t kH = kXe + kXeBytes;           // pass-2 operand planes
-  static constexpr uint32_t kHBytes = kTile * kWin * E;
-  static constexpr uint32_t kOut = kH + NPLANES * kHBytes; // output staging x2
+  static constexpr uint32_t kXe = kXs + NS * kXsBytes;        // encoded window
+  static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E1 : 0;
+  static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand
+  static constexpr uint32_t kHBytes = kTile * kWin * 2;
+  static constexpr uint32_t kOut = kH + kHBytes;              // output staging x2
   static constexpr uint32_t kOutBytes = kTile * kTile;
   static constexpr uint32_t kBars = kOut + 2 * kOutBytes;
-  static constexpr uint32_t kTotal = kBars + 512;
-  static constexpr uint32_t kDyn = kTotal + 1024;          // + alignment slack
+  static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
 };
 
 struct Bars {
@@ -101,7 +118,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *
   return __all_sync(0xffffffffu, ok);
 }
 
-// Encodes the 160 x 160 u8 window xs as operand values (1 -> one, else 0).
+// Encodes the 160 x 160 u8 window xs as operand values: alive (state 1) ->
+// 0x01 (e4m3 2^-9, FP8 kernel) or f16 1.0 (FP16 kernel), anything else -> 0.
 template <int E>
 __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bool multistate,
                                               int tid, int nthr) {
@@ -114,14 +132,12 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
       for (int i = 0; i < 4; ++i) w[i] = __vcmpeq4(w[i], 0x01010101u) & 0x01010101u;
     }
     if constexpr (E == 1) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) w[i] *= 0x38u;  // e4m3 1.0
       *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
       uint32_t h[8];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        h[2 * i] = __byte_perm(w[i], 0, 0x4140) * 0x3C00u;      // fp16 1.0 per 0/1 byte
+        h[2 * i] = __byte_perm(w[i], 0, 0x4140) * 0x3C00u;
         h[2 * i + 1] = __byte_perm(w[i], 0, 0x4342) * 0x3C00u;
       }
       *reinterpret_cast<uint4 *>(xe + op_off(kWin, 2, row, 32 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -152,9 +168,14 @@ __device__ __forceinline__ void build_band(uint8_t *band, int r, int tid, int nt
   }
 }
 
-__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+__device__ __forceinline__ uint32_t f16x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
+  __half2 h = __floats2half2_rn(__uint_as_float(lo_f32), __uint_as_float(hi_f32));
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t e4m3x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
   uint16_t r;
-  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(__uint_as_float(hi_f32)), "f"(__uint_as_float(lo_f32)));
   return r;
 }
 
@@ -163,6 +184,45 @@ __device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev 
   if (c == 0) return (uint32_t)(s - R.b_lo) <= (uint32_t)R.b_w;
   if (c == 1) return ((uint32_t)(s - R.s_lo) <= (uint32_t)R.s_w) ? 1u : (R.C > 2 ? 2u : 0u);
   return (c + 1 == (uint32_t)R.C) ? 0u : c + 1;
+}
+
+// The rule's two ranges as f16 pairs, scaled like the accumulator (S * scale).
+// A lower bound above any count (1089) makes the range empty; an upper bound
+// above it is clamped to 2048.  All values are exact in f16.
+struct HalfRule {
+  uint32_t bl2, bh2, sl2, sh2;
+};
+
+__device__ __forceinline__ uint32_t half_pair(float v) {
+  __half2 h = __float2half2_rn(v);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ HalfRule make_half_rule(const RuleDev &R, float scale) {
+  auto lo_of = [](int lo) { return lo > 1089 ? 4096.0f : (float)lo; };
+  auto hi_of = [](int lo, int w) { return lo > 1089 ? 2048.0f : fminf((float)lo + (float)w, 2048.0f); };
+  HalfRule h;
+  h.bl2 = half_pair(lo_of(R.b_lo) * scale);
+  h.bh2 = half_pair(hi_of(R.b_lo, R.b_w) * scale);
+  h.sl2 = half_pair(lo_of(R.s_lo) * scale);
+  h.sh2 = half_pair(hi_of(R.s_lo, R.s_w) * scale);
+  return h;
+}
+
+__device__ __forceinline__ __half2 as_h2(uint32_t v) { return *reinterpret_cast<const __half2 *>(&v); }
+
+// 4 next states (C == 2) from 4 accumulator values and 4 centre bytes (0/1).
+// The centre bits pick each cell's bounds with one byte permute: selector
+// nibbles 0..3 take the birth pair, 4..7 the survival pair.
+__device__ __forceinline__ uint32_t rule4_binary(const uint32_t *v, uint32_t cw, const HalfRule &h) {
+  const uint32_t selA = cw * 0x44u + 0x3210u;          // cells 0, 1 (low 16 bits used)
+  const uint32_t selB = (cw >> 16) * 0x44u + 0x3210u;  // cells 2, 3
+  const __half2 s01 = as_h2(f16x2_bits(v[0], v[1])), s23 = as_h2(f16x2_bits(v[2], v[3]));
+  const uint32_t m01 = __hge2_mask(s01, as_h2(__byte_perm(h.bl2, h.sl2, selA))) &
+                       __hle2_mask(s01, as_h2(__byte_perm(h.bh2, h.sh2, selA)));
+  const uint32_t m23 = __hge2_mask(s23, as_h2(__byte_perm(h.bl2, h.sl2, selB))) &
+                       __hle2_mask(s23, as_h2(__byte_perm(h.bh2, h.sh2, selB)));
+  return __byte_perm(m01, m23, 0x6420) & 0x01010101u;
 }
 
 // What one output tile needs: its maps, origin, grid extent and rule.
@@ -220,15 +280,16 @@ __device__ __forceinline__ Tile get_tile(const TcParams &p, int first, int j) {
   return t;
 }
 
-__device__ __forceinline__ int planes_for(int DT, int r) { return (DT == 1 && 2 * r + 1 > 15) ? 2 : 1; }
+// Pass 2 reads f16 in the FP16 kernel and, in the FP8 kernel, whenever H can
+// exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
+__device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
 template <int DT, bool ENC, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
-  constexpr int E = DT == 0 ? 2 : 1;            // operand bytes (FP16 / FP8 e4m3)
-  constexpr int NS = DT == 0 ? 2 : 3;           // TMA window stages
-  constexpr int NPLANES = DT == 0 ? 1 : 2;      // pass-2 operand planes
-  constexpr int KSTEPS = 5 * E;                 // 160 / (32 / E)
-  using L = Layout<E, NS, ENC, NPLANES>;
+  using L = Layout<DT, ENC>;
+  constexpr int E1 = L::E1;
+  constexpr int NS = L::NS;
+  constexpr float kScale = DT == 1 ? (1.0f / 512.0f) : 1.0f;   // accumulator = count * kScale
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -236,11 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int first, n_my;
   my_range<BATCH>(p, first, n_my);
-  const float d1_scale = (DT == 1 && !ENC) ? 512.0f : 1.0f;     // raw 0x01 byte = e4m3 2^-9
   int32_t *err0 = BATCH ? (n_my > 0 ? get_tile<BATCH>(p, first, 0).err : nullptr) : p.err;
   const int r0 = n_my > 0 ? get_tile<BATCH>(p, first, 0).R.r : 1;
 
-  // ---- set-up: barriers, TMEM, band ------------------------------------
+  // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
     for (int i = 0; i < 3; ++i) { mbar_init(&bars->x_full[i], 1); mbar_init(&bars->x_empty[i], kWorkerWarps); }
     for (int i = 0; i < kRegions; ++i) {
@@ -261,7 +321,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     tmem_alloc(&bars->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  build_band<E>(smem + L::kBand, r0, threadIdx.x, kThreads);
+  build_band<2>(smem + L::kBand16, r0, threadIdx.x, kThreads);
+  if (DT == 1) build_band<1>(smem + L::kBand8, r0, threadIdx.x, kThreads);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -294,7 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     if (lane == 0) {
       const uint32_t idesc1 = idesc_f32acc(128, kWin);
       const uint32_t idesc2 = idesc_f32acc(128, kTile);
-      const uint32_t band = s_base + L::kBand;
+      const uint32_t band1 = s_base + (DT == 1 ? L::kBand8 : L::kBand16);
+      const uint32_t band16 = s_base + L::kBand16, band8 = s_base + L::kBand8;
+      const uint32_t hop = s_base + L::kH;
       bool ok = true;
       int band_r = r0, prev_r = r0, rebuilds = 0;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -306,15 +369,14 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         if (!mbar_wait(&bars->h_full, jj & 1, &bars->abort, p.timeout_ns)) return false;
         tc_fence_after();
         const uint32_t d2 = tmem + reg * kRegionCols;
-        const int nplanes = planes_for(DT, r);
-        for (int pl = 0; pl < nplanes; ++pl) {
-          const uint32_t hop = s_base + L::kH + pl * L::kHBytes;
+        if (pass2_f16(DT, r)) {
 #pragma unroll
-          for (int k = 0; k < KSTEPS; ++k) {
-            const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(hop, kTile, E, k);
-            if constexpr (DT == 0) mma_f16(d2, a, b, idesc2, (pl | k) > 0);
-            else mma_f8f6f4(d2, a, b, idesc2, (pl | k) > 0);
-          }
+          for (int k = 0; k < 10; ++k)
+            mma_f16(d2, op_desc(band16, kTile, 2, k), op_desc(hop, kTile, 2, k), idesc2, k > 0);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 5; ++k)
+            mma_f8f6f4(d2, op_desc(band8, kTile, 1, k), op_desc(hop, kTile, 1, k), idesc2, k > 0);
         }
         mma_commit(&bars->d2_full[reg]);
         return true;
@@ -343,8 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
           const uint32_t d1 = tmem + reg * kRegionCols;
 #pragma unroll
-          for (int k = 0; k < KSTEPS; ++k) {
-            const uint64_t a = op_desc(band, kTile, E, k), b = op_desc(win, kWin, E, k);
+          for (int k = 0; k < 5 * E1; ++k) {
+            const uint64_t a = op_desc(band1, kTile, E1, k), b = op_desc(win, kWin, E1, k);
             if constexpr (DT == 0) mma_f16(d1, a, b, idesc1, k > 0);
             else mma_f8f6f4(d1, a, b, idesc1, k > 0);
           }
@@ -362,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
   } else {
     // --------------------------------------------------------------- workers
-    const int wtid = threadIdx.x - 64;            // 0..255
+    const int wtid = threadIdx.x - 64;            // 0 .. kWorkerThreads-1
     const int q = warp & 3;                       // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;             // which half of the columns
+    const int kq = (warp - 2) >> 2;               // 0..3: which warp of the quarter
     const int row = 32 * q + lane;                // TMEM lane = x (pass 1) / y (pass 2)
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
     const bool store_thread = wtid == 0;
@@ -375,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const Tile t0 = get_tile<BATCH>(p, first, 0);
       ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
       if (ok) {
-        encode_window<E>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, 32 * kWorkerWarps);
+        encode_window<E1>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, kWorkerThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
@@ -387,55 +449,45 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const RuleDev &R = t.R;
       const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
       const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
-      const int nplanes = planes_for(DT, R.r);
+      const bool p2f16 = pass2_f16(DT, R.r);
 
-      // ---- new radius: every MMA on the old band has completed (EPI of j-1 saw it)
+      // ---- new radius: every MMA on the old bands has completed (EPI of j-1 saw it)
       if (BATCH && R.r != band_r) {
-        build_band<E>(smem + L::kBand, R.r, wtid, 32 * kWorkerWarps);
+        build_band<2>(smem + L::kBand16, R.r, wtid, kWorkerThreads);
+        if (DT == 1) build_band<1>(smem + L::kBand8, R.r, wtid, kWorkerThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
         band_r = R.r;
       }
 
-      // ---- D1 (H^T) -> pass-2 operand
+      // ---- D1 (H^T, lane x, columns y') -> pass-2 operand row x
       if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       {
-        uint32_t v[5][16];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) tmem_ld16(treg + 16 * (5 * half + c), v[c]);
+        // chunks of 16 columns: warp kq of the quarter takes kq, kq+4, kq+8 (< 10)
+        uint32_t v[3][16];
+        const int nch = kq < 2 ? 3 : 2;
+        tmem_ld16(treg + 16 * kq, v[0]);
+        tmem_ld16(treg + 16 * (kq + 4), v[1]);
+        if (nch == 3) tmem_ld16(treg + 16 * (kq + 8), v[2]);
         tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          const int cc = 5 * half + c;  // columns y' = 16cc .. 16cc+15
-          if constexpr (E == 2) {
+        for (int c = 0; c < 3; ++c) {
+          if (c >= nch) break;
+          const int cc = kq + 4 * c;  // columns y' = 16cc .. 16cc+15
+          if (p2f16) {
             uint32_t h[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              __half2 hv = __floats2half2_rn(__uint_as_float(v[c][2 * i]), __uint_as_float(v[c][2 * i + 1]));
-              h[i] = *reinterpret_cast<uint32_t *>(&hv);
-            }
+            for (int i = 0; i < 8; ++i) h[i] = f16x2_bits(v[c][2 * i], v[c][2 * i + 1]);
             *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc)) = make_uint4(h[0], h[1], h[2], h[3]);
             *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc + 16)) = make_uint4(h[4], h[5], h[6], h[7]);
           } else {
-            uint32_t lo[4], hi[4];
+            uint32_t e[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              float f[4], fl[4], fh[4];
-#pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                f[b] = __uint_as_float(v[c][4 * i + b]) * d1_scale;
-                fh[b] = nplanes == 2 ? floorf(f[b] * 0.0625f) * 16.0f : 0.0f;  // 0, 16 or 32
-                fl[b] = f[b] - fh[b];                                          // 0..15
-              }
-              lo[i] = e4m3x2(fl[0], fl[1]) | (e4m3x2(fl[2], fl[3]) << 16);
-              hi[i] = e4m3x2(fh[0], fh[1]) | (e4m3x2(fh[2], fh[3]) << 16);
-            }
-            const uint32_t off = op_off(kTile, 1, row, 16 * cc);
-            *reinterpret_cast<uint4 *>(hop + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            if (nplanes == 2)
-              *reinterpret_cast<uint4 *>(hop + L::kHBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            for (int i = 0; i < 4; ++i)
+              e[i] = e4m3x2_bits(v[c][4 * i], v[c][4 * i + 1]) | (e4m3x2_bits(v[c][4 * i + 2], v[c][4 * i + 3]) << 16);
+            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 1, row, 16 * cc)) = make_uint4(e[0], e[1], e[2], e[3]);
           }
         }
       }
@@ -449,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const int s1 = (j + 1) % NS;
         const bool ms1 = get_tile<BATCH>(p, first, j + 1).R.C > 2;
         if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
-        encode_window<E>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, 32 * kWorkerWarps);
+        encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kWorkerThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
@@ -464,48 +516,55 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       }
       if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p.timeout_ns))) break;
       uint8_t *out = smem + L::kOut + o * L::kOutBytes;
-      const bool multistate = R.C > 2;
       {
-        uint32_t v[4][16];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tmem_ld16(treg + 16 * (4 * half + c), v[c]);
+        // chunks of 16 columns x: warp kq takes kq and kq + 4
+        uint32_t v[2][16];
+        tmem_ld16(treg + 16 * kq, v[0]);
+        tmem_ld16(treg + 16 * (kq + 4), v[1]);
         tmem_wait_ld();
         const int y = row;
+        const bool sums_mode = !BATCH && p.sums != nullptr;
+        if (!sums_mode && R.C == 2) {
+          const HalfRule hr = make_half_rule(R, kScale);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int cc = 4 * half + c;  // x = 16cc .. 16cc+15
-          const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
-          const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
-          if (!BATCH && p.sums) {
-            const int gy = t.y0 + y;
+          for (int c = 0; c < 2; ++c) {
+            const int cc = kq + 4 * c;
+            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
+            uint4 ov;
+            ov.x = rule4_binary(&v[c][0], cv.x, hr);
+            ov.y = rule4_binary(&v[c][4], cv.y, hr);
+            ov.z = rule4_binary(&v[c][8], cv.z, hr);
+            ov.w = rule4_binary(&v[c][12], cv.w, hr);
+            *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = ov;
+          }
+        } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int gx = t.x0 + 16 * cc + i;
-              if (gy < t.H && gx < t.W)
-                p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]));
-            }
-          } else {
-            uint32_t ow[4];
+          for (int c = 0; c < 2; ++c) {
+            const int cc = kq + 4 * c;
+            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
+            const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
+            if (sums_mode) {
+              const int gy = t.y0 + y;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              uint32_t word = 0;
-#pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const int s_cnt = __float2int_rn(__uint_as_float(v[c][4 * i + b]));
-                const uint32_t st = (cw[i] >> (8 * b)) & 0xFFu;
-                uint32_t nx;
-                if (!multistate) {
-                  const int lo = st ? R.s_lo : R.b_lo;
-                  const int wd = st ? R.s_w : R.b_w;
-                  nx = (uint32_t)(s_cnt - lo) <= (uint32_t)wd;
-                } else {
-                  nx = next_state(s_cnt, st, R);
-                }
-                word |= nx << (8 * b);
+              for (int i = 0; i < 16; ++i) {
+                const int gx = t.x0 + 16 * cc + i;
+                if (gy < t.H && gx < t.W)
+                  p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]) * (1.0f / kScale));
               }
-              ow[i] = word;
+            } else {
+              uint32_t ow[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  const int s_cnt = __float2int_rn(__uint_as_float(v[c][4 * i + b]) * (1.0f / kScale));
+                  word |= next_state(s_cnt, (cw[i] >> (8 * b)) & 0xFFu, R) << (8 * b);
+                }
+                ow[i] = word;
+              }
+              *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
             }
-            *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
           }
         }
       }
@@ -540,14 +599,16 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 
 }  // namespace tc
 
+// dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
 size_t tc_smem_bytes(int dt, bool encode) {
-  if (dt == 1) return tc::Layout<2, 2, true, 1>::kDyn;
-  return encode ? tc::Layout<1, 3, true, 2>::kDyn : tc::Layout<1, 3, false, 2>::kDyn;
+  if (dt == 1) return tc::Layout<0, true>::kDyn;
+  return encode ? tc::Layout<1, true>::kDyn : tc::Layout<1, false>::kDyn;
 }
 
 template <int DT, bool ENC, bool BATCH>
-static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, size_t smem) {
+static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
   static bool configured = false;
+  const size_t smem = tc::Layout<DT, ENC>::kDyn;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -558,17 +619,16 @@ static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, size_
   return cudaGetLastError();
 }
 
-// dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
-  if (dt == 1) return launch_one<0, true, false>(p, grid, s, tc_smem_bytes(1, true));
-  if (encode) return launch_one<1, true, false>(p, grid, s, tc_smem_bytes(2, true));
-  return launch_one<1, false, false>(p, grid, s, tc_smem_bytes(2, false));
+  if (dt == 1) return launch_one<0, true, false>(p, grid, s);
+  if (encode) return launch_one<1, true, false>(p, grid, s);
+  return launch_one<1, false, false>(p, grid, s);
 }
 
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
-  if (dt == 1) return launch_one<0, true, true>(p, grid, s, tc_smem_bytes(1, true));
-  if (encode) return launch_one<1, true, true>(p, grid, s, tc_smem_bytes(2, true));
-  return launch_one<1, false, true>(p, grid, s, tc_smem_bytes(2, false));
+  if (dt == 1) return launch_one<0, true, true>(p, grid, s);
+  if (encode) return launch_one<1, true, true>(p, grid, s);
+  return launch_one<1, false, true>(p, grid, s);
 }
 
 }  // namespace cat
