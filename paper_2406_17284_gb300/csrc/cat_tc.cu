@@ -123,8 +123,10 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *
 template <int E>
 __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bool multistate,
                                               int tid, int nthr) {
+  // consecutive threads take consecutive rows of one 16-byte column chunk, so
+  // every warp access touches each bank group evenly under both swizzles
   for (int q = tid; q < kWin * 10; q += nthr) {
-    const int row = q / 10, c = q - row * 10;
+    const int c = q / kWin, row = q - c * kWin;
     uint4 v = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, row, 16 * c));
     uint32_t w[4] = {v.x, v.y, v.z, v.w};
     if (multistate) {
@@ -433,6 +435,23 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     uint8_t *hop = smem + L::kH;
     bool ok = true;
     int band_r = r0;
+    // this thread's shared-memory offsets, fixed for every tile
+    const int nch = kq < 2 ? 3 : 2;               // D1 column chunks kq, kq+4, kq+8 (< 10)
+    uint32_t off16a[3], off16b[3], off8[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int cc = kq + 4 * c < 10 ? kq + 4 * c : kq;
+      off16a[c] = op_off(kTile, 2, row, 32 * cc);
+      off16b[c] = op_off(kTile, 2, row, 32 * cc + 16);
+      off8[c] = op_off(kTile, 1, row, 16 * cc);
+    }
+    uint32_t off_ctr[2], off_out[2];               // D2 column chunks kq, kq+4
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = kq + 4 * c;
+      off_ctr[c] = op_off(kWin, 1, row + 16, 16 * cc + 16);
+      off_out[c] = row * 128 + (((cc ^ row) & 7) << 4);
+    }
     if (ENC && n_my > 0) {
       const Tile t0 = get_tile<BATCH>(p, first, 0);
       ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
@@ -467,7 +486,6 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       {
         // chunks of 16 columns: warp kq of the quarter takes kq, kq+4, kq+8 (< 10)
         uint32_t v[3][16];
-        const int nch = kq < 2 ? 3 : 2;
         tmem_ld16(treg + 16 * kq, v[0]);
         tmem_ld16(treg + 16 * (kq + 4), v[1]);
         if (nch == 3) tmem_ld16(treg + 16 * (kq + 8), v[2]);
@@ -475,19 +493,18 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (c >= nch) break;
-          const int cc = kq + 4 * c;  // columns y' = 16cc .. 16cc+15
           if (p2f16) {
             uint32_t h[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) h[i] = f16x2_bits(v[c][2 * i], v[c][2 * i + 1]);
-            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc)) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 2, row, 32 * cc + 16)) = make_uint4(h[4], h[5], h[6], h[7]);
+            *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(h[4], h[5], h[6], h[7]);
           } else {
             uint32_t e[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
               e[i] = e4m3x2_bits(v[c][4 * i], v[c][4 * i + 1]) | (e4m3x2_bits(v[c][4 * i + 2], v[c][4 * i + 3]) << 16);
-            *reinterpret_cast<uint4 *>(hop + op_off(kTile, 1, row, 16 * cc)) = make_uint4(e[0], e[1], e[2], e[3]);
+            *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
           }
         }
       }
@@ -528,20 +545,19 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           const HalfRule hr = make_half_rule(R, kScale);
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const int cc = kq + 4 * c;
-            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
+            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
             uint4 ov;
             ov.x = rule4_binary(&v[c][0], cv.x, hr);
             ov.y = rule4_binary(&v[c][4], cv.y, hr);
             ov.z = rule4_binary(&v[c][8], cv.z, hr);
             ov.w = rule4_binary(&v[c][12], cv.w, hr);
-            *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = ov;
+            *reinterpret_cast<uint4 *>(out + off_out[c]) = ov;
           }
         } else {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int cc = kq + 4 * c;
-            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, y + 16, 16 * cc + 16));
+            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
             const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
             if (sums_mode) {
               const int gy = t.y0 + y;
@@ -563,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
                 }
                 ow[i] = word;
               }
-              *reinterpret_cast<uint4 *>(out + y * 128 + (((cc ^ y) & 7) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+              *reinterpret_cast<uint4 *>(out + off_out[c]) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
             }
           }
         }

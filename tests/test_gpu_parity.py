@@ -226,3 +226,55 @@ def test_bounded_wait_reports_timeout_and_context_survives(cat):
         assert_same(g.get_state(), want, "after timeout")
     finally:
         g.close()
+
+
+# ------------------------------------------------- workload-scale parity cases
+@pytest.mark.parametrize("dtype", ["fp8", "fp16"])
+def test_radius_sweep_4096_every_radius(cat, dtype):
+    """4096^2 Bernoulli(0.5), the radius-scaled rule (C2 M1) for r = 1..16, 2 steps, full equality."""
+    grid = inputs.bernoulli(4096, 4096, 0.5, 4096)
+    for r in range(1, 17):
+        rule = rule_dict(r, M=1)
+        want = _oracle_run(4096, 4096, 0.5, 4096, tuple(rule.items()), 2)
+        assert_same(run_gpu(cat, "tcgen05", dtype, grid, rule, 2), want, f"4096^2 r={r}")
+
+
+def test_cross_dtype_equality_after_many_steps(cat):
+    """Every kernel/dtype reaches the same state after 20 steps on 2048^2 (p = 0.35)."""
+    grid = inputs.bernoulli(2048, 2048, 0.35, 35)
+    for r in (1, 5, 10, 16):
+        rule = rule_dict(r, M=1)
+        outs = {f"{k}/{d}": run_gpu(cat, k, d, grid, rule, 20) for k, d in KERNELS}
+        ref = outs["tcgen05/fp16"]
+        for name, o in outs.items():
+            assert_same(o, ref, f"r={r} {name} vs tcgen05/fp16")
+        # and the oracle agrees after the same 20 steps
+        want = oracle.step(grid, orule(rule), n_steps=20)
+        assert_same(ref, want, f"r={r} oracle")
+
+
+def test_multistate_r10_c16_windows(cat):
+    """R10 C16 M1 S150..260 B150..200, states uniform over {0..15}, 4096^2; after
+    every 25 steps one step is checked on 8 windows against the oracle."""
+    import torch
+    N, C = 4096, 16
+    rule = inputs.MULTISTATE_R10_C16
+    g = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8")
+    rng = np.random.default_rng(16)
+    try:
+        g.set_state(inputs.uniform_states(N, N, C, 1616))
+        for block in range(4):
+            g.step(24)
+            before = g.state_tensor().cpu().numpy().copy()
+            g.step(1)
+            after = g.state_tensor().cpu().numpy()
+            assert g.status() == cat.CAT_OK
+            for _ in range(8):
+                y0, x0 = (int(v) for v in rng.integers(0, N - 128, 2))
+                ya, xa = max(0, y0 - 10), max(0, x0 - 10)
+                win = before[ya:min(N, y0 + 138), xa:min(N, x0 + 138)]
+                want = oracle.step(win, orule(rule))[y0 - ya:y0 - ya + 128, x0 - xa:x0 - xa + 128]
+                assert_same(after[y0:y0 + 128, x0:x0 + 128], want, f"block {block} window ({y0},{x0})")
+            assert int((after >= 2).sum()) > 0  # decaying states are present
+    finally:
+        g.close()
