@@ -150,6 +150,50 @@ CAT_API int cat_box_sums(cat_handle_t h, int32_t *dst, int64_t ld, void *stream)
  * then skipped its remaining tiles), else CAT_OK.  Clears the flag.         */
 CAT_API int cat_status(cat_handle_t h, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free batched step.  The paper has no counterpart to this call.
+ *
+ * cat_batch_step allocates device memory for its descriptor table and tile
+ * work-list.  Some callers cannot allow that: a framework whose caching
+ * allocator already owns the whole device-memory budget, a service whose
+ * memory footprint is fixed when it starts, or code that must not call
+ * cudaMalloc/cudaFree because those calls can synchronise the device.
+ * cat_batch_step_static advances `count` independent grids by ONE step in one
+ * persistent tcgen05 launch and allocates nothing: the caller passes the input
+ * and output buffers (device memory, e.g. from its own allocator), and the
+ * table and work-list go into one fixed array compiled into the library
+ * (753,792 bytes = about 736 KiB of device memory, held on every GPU that loads the library
+ * until the process exits).
+ *
+ *  - Limits: at most CAT_STATIC_MAX_GRIDS grids and CAT_STATIC_MAX_TILES tiles
+ *    of 128 x 128 cells in total; larger batches get CAT_ERR_INVALID_ARG and
+ *    nothing is launched.  Each grid: 1 <= H, W <= 4194176, pitch >= W and a
+ *    multiple of 16 bytes, 16-byte aligned buffers, `in` != `out`.
+ *  - dtype: CAT_DTYPE_FP8_E4M3 (or AUTO) or CAT_DTYPE_FP16.
+ *  - d_status: optional device int32 that receives 0, or a non-zero code if a
+ *    bounded device wait timed out; it is zeroed at the start of the call.
+ *  - The first call on a device finds the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call reuses the same array, which keeps the last call's contents.
+ *    Calls whose launches overlap on the GPU (e.g. on two streams without an
+ *    ordering between them) race on it: order them on one stream.
+ *  - The next states are written to `out`; swap `in` and `out` to continue.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.                                    */
+#define CAT_STATIC_MAX_GRIDS 256
+#define CAT_STATIC_MAX_TILES 65536
+
+typedef struct cat_grid_desc {
+  const uint8_t *in; /* current states (device memory), H rows at `pitch` bytes */
+  uint8_t *out;      /* next states (device memory), same layout               */
+  int64_t H, W;      /* rows and columns                                      */
+  int64_t pitch;     /* bytes between consecutive rows of both buffers        */
+  cat_rule_t rule;
+} cat_grid_desc_t;
+
+CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32_t count, int32_t dtype,
+                                  int32_t *d_status, void *stream);
+
 /* Test hook for the failure-detection path; not needed in normal use.
  *   what = 1: value 1 makes the next tcgen05 launches wait on a barrier that
  *             nothing arrives at, so the bounded wait runs out (value 0 clears);

@@ -36,11 +36,19 @@ KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MM
 
 EXPORTED = ["cat_create", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
             "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
-            "cat_destroy", "cat_last_error", "cat_version"]
+            "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static"]
+
+CAT_STATIC_MAX_GRIDS = 256
+CAT_STATIC_MAX_TILES = 65536
 
 
 class cat_rule_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("r", "C", "M", "s1", "s2", "b1", "b2", "nbhd")]
+
+
+class cat_grid_desc_t(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int64),
+                ("W", ctypes.c_int64), ("pitch", ctypes.c_int64), ("rule", cat_rule_t)]
 
 
 class CatError(RuntimeError):
@@ -86,6 +94,7 @@ def load(path: str | None = None):
             "cat_destroy": [h],
             "cat_last_error": [],
             "cat_version": [],
+            "cat_batch_step_static": [ctypes.POINTER(cat_grid_desc_t), i32, i32, p, p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -165,6 +174,13 @@ def cat_debug_control(h: int, what: int, value: int):
 
 def cat_destroy(h: int):
     _check(load().cat_destroy(h))
+
+
+def cat_batch_step_static(descs: list, dtype: int = DTYPE_FP8_E4M3, status_ptr: int | None = None,
+                          stream=None) -> int:
+    """One step of every grid in `descs` (cat_grid_desc_t) without device allocation."""
+    arr = (cat_grid_desc_t * len(descs))(*descs)
+    return load().cat_batch_step_static(arr, len(descs), dtype, status_ptr, _stream_ptr(stream))
 
 
 def cat_version() -> str:

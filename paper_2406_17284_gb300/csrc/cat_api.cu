@@ -302,6 +302,18 @@ int launch_batch_steps(BatchPlan *pl, int64_t n_steps, int64_t start, cudaStream
 
 }  // namespace
 
+// Host helpers shared with the allocation-free entry point (cat_static.cu).
+namespace cat {
+int host_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int host_validate_rule(const cat_rule_t *r) { return validate_rule(r); }
+RuleDev host_reduce_rule(const cat_rule_t &r) { return reduce_rule(r); }
+int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, uint32_t box_x,
+                  uint32_t box_y, int swizzle128) {
+  return make_map(m, base, H, W, pitch, box_x, box_y,
+                  swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+}  // namespace cat
+
 extern "C" {
 
 const char *cat_last_error(void) { return g_err; }

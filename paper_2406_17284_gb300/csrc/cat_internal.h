@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "../../include/cat.h"
+
 namespace cat {
 
 // LTL rule reduced to range tests on the box count S (centre included).
@@ -75,6 +77,14 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
 size_t tc_smem_bytes(int dt, bool encode);
+
+// Host helpers defined in cat_api.cu (error message of the calling thread,
+// rule checks, TMA descriptor encoding of a uint8 grid).
+int host_fail(int code, const char *msg);
+int host_validate_rule(const cat_rule_t *r);
+RuleDev host_reduce_rule(const cat_rule_t &r);
+int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, uint32_t box_x,
+                  uint32_t box_y, int swizzle128);
 
 // Paper-style fragment kernels (cat_mma.cu).  dt: FP16 or INT8.
 cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s);
