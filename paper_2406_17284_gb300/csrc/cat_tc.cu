@@ -30,10 +30,10 @@
 // The epilogue compares S (as f16, exact up to 2048) against the rule's
 // ranges two cells at a time in half2 arithmetic.
 //
-// Roles (576 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
-// issuer, warps 2..17 = workers (four per TMEM lane quarter): D1 -> pass-2
-// operand, window encoding when needed, and the fused transition epilogue with
-// the TMA store.  Every wait is bounded; on timeout the CTA records
+// Roles (704 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
+// issuer, warps 2..9 = convert warps (D1 -> pass-2 operand, window encoding
+// when needed, band rebuilds), warps 10..21 = epilogue warps (fused transition
+// and TMA store).  The two worker roles work on different tiles at once.  Every wait is bounded; on timeout the CTA records
 // kDevErrTimeout, drains its own in-flight copies and MMAs, frees TMEM and
 // returns.
 #include <cuda_fp16.h>
@@ -46,9 +46,11 @@ namespace tc {
 
 constexpr int kTile = 128;
 constexpr int kWin = 160;
-constexpr int kWorkerWarps = 16;
-constexpr int kWorkerThreads = 32 * kWorkerWarps;
-constexpr int kThreads = 64 + kWorkerThreads;
+constexpr int kCvtWarps = 8;                       // two per TMEM lane quarter
+constexpr int kEpiWarps = 12;                      // three per TMEM lane quarter
+constexpr int kCvtThreads = 32 * kCvtWarps;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kCvtThreads + kEpiThreads;
 constexpr int kRegions = 3;
 constexpr int kRegionCols = 160;
 constexpr uint32_t kTmemCols = 512;
@@ -304,16 +306,16 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) { mbar_init(&bars->x_full[i], 1); mbar_init(&bars->x_empty[i], kWorkerWarps); }
+    for (int i = 0; i < 3; ++i) { mbar_init(&bars->x_full[i], 1); mbar_init(&bars->x_empty[i], kEpiWarps); }
     for (int i = 0; i < kRegions; ++i) {
       mbar_init(&bars->d1_full[i], 1);
       mbar_init(&bars->d2_full[i], 1);
-      mbar_init(&bars->tmem_empty[i], kWorkerWarps);
+      mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
-    mbar_init(&bars->h_full, kWorkerWarps);
-    mbar_init(&bars->enc_full, kWorkerWarps);
-    mbar_init(&bars->band_ready, kWorkerWarps);
-    for (int i = 0; i < 2; ++i) { mbar_init(&bars->out_free[i], 1); mbar_init(&bars->out_full[i], kWorkerWarps); }
+    mbar_init(&bars->h_full, kCvtWarps);
+    mbar_init(&bars->enc_full, kCvtWarps);
+    mbar_init(&bars->band_ready, kCvtWarps);
+    for (int i = 0; i < 2; ++i) { mbar_init(&bars->out_free[i], 1); mbar_init(&bars->out_full[i], kEpiWarps); }
     mbar_init(&bars->mma_done, 1);
     mbar_init(&bars->never, 1);
     bars->abort = 0;
@@ -424,87 +426,78 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       volatile int no_abort = 0;
       if (!mbar_wait(&bars->mma_done, 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 6);
     }
-  } else {
-    // --------------------------------------------------------------- workers
-    const int wtid = threadIdx.x - 64;            // 0 .. kWorkerThreads-1
+  } else if (warp < 2 + kCvtWarps) {
+    // ------------------------------------------------- convert warps (2 .. 9)
+    // D1 (H^T, lane x, columns y') -> K-major pass-2 operand; window encoding
+    // for the next tile; band rebuilds when the radius changes (batch mode).
+    const int wtid = threadIdx.x - 64;            // 0 .. kCvtThreads-1
     const int q = warp & 3;                       // TMEM lane quarter of this warp
-    const int kq = (warp - 2) >> 2;               // 0..3: which warp of the quarter
-    const int row = 32 * q + lane;                // TMEM lane = x (pass 1) / y (pass 2)
+    const int kq = (warp - 2) >> 2;               // 0..1: which warp of the quarter
+    const int row = 32 * q + lane;                // TMEM lane = x
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
-    const bool store_thread = wtid == 0;
     uint8_t *hop = smem + L::kH;
     bool ok = true;
     int band_r = r0;
-    // this thread's shared-memory offsets, fixed for every tile
-    const int nch = kq < 2 ? 3 : 2;               // D1 column chunks kq, kq+4, kq+8 (< 10)
-    uint32_t off16a[3], off16b[3], off8[3];
+    // this thread's operand offsets: D1 column chunks 5kq .. 5kq+4 (16 columns each)
+    uint32_t off16a[5], off16b[5], off8[5];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int cc = kq + 4 * c < 10 ? kq + 4 * c : kq;
+    for (int c = 0; c < 5; ++c) {
+      const int cc = 5 * kq + c;
       off16a[c] = op_off(kTile, 2, row, 32 * cc);
       off16b[c] = op_off(kTile, 2, row, 32 * cc + 16);
       off8[c] = op_off(kTile, 1, row, 16 * cc);
-    }
-    uint32_t off_ctr[2], off_out[2];               // D2 column chunks kq, kq+4
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int cc = kq + 4 * c;
-      off_ctr[c] = op_off(kWin, 1, row + 16, 16 * cc + 16);
-      off_out[c] = row * 128 + (((cc ^ row) & 7) << 4);
     }
     if (ENC && n_my > 0) {
       const Tile t0 = get_tile<BATCH>(p, first, 0);
       ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
       if (ok) {
-        encode_window<E1>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, kWorkerThreads);
+        encode_window<E1>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
       }
     }
     for (int j = 0; ok && j < n_my; ++j) {
-      const int reg = j % kRegions, s = j % NS, o = j & 1;
+      const int reg = j % kRegions;
       const Tile t = get_tile<BATCH>(p, first, j);
-      const RuleDev &R = t.R;
-      const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
-      const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
-      const bool p2f16 = pass2_f16(DT, R.r);
-
-      // ---- new radius: every MMA on the old bands has completed (EPI of j-1 saw it)
-      if (BATCH && R.r != band_r) {
-        build_band<2>(smem + L::kBand16, R.r, wtid, kWorkerThreads);
-        if (DT == 1) build_band<1>(smem + L::kBand8, R.r, wtid, kWorkerThreads);
+      const bool p2f16 = pass2_f16(DT, t.R.r);
+      // pass 2 of tile j-1 has finished reading H (and, if the radius changes, the bands)
+      if (j >= 1 && !(ok = warp_wait(&bars->d2_full[(j - 1) % kRegions], ((j - 1) / kRegions) & 1, bars, p.timeout_ns))) break;
+      if (BATCH && t.R.r != band_r) {
+        build_band<2>(smem + L::kBand16, t.R.r, wtid, kCvtThreads);
+        if (DT == 1) build_band<1>(smem + L::kBand8, t.R.r, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
-        band_r = R.r;
+        band_r = t.R.r;
       }
-
-      // ---- D1 (H^T, lane x, columns y') -> pass-2 operand row x
       if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       {
-        // chunks of 16 columns: warp kq of the quarter takes kq, kq+4, kq+8 (< 10)
-        uint32_t v[3][16];
-        tmem_ld16(treg + 16 * kq, v[0]);
-        tmem_ld16(treg + 16 * (kq + 4), v[1]);
-        if (nch == 3) tmem_ld16(treg + 16 * (kq + 8), v[2]);
-        tmem_wait_ld();
+        const uint32_t treg = tmem + lane_addr + reg * kRegionCols + 80 * kq;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (c >= nch) break;
-          if (p2f16) {
-            uint32_t h[8];
+        for (int c0 = 0; c0 < 5; c0 += 2) {        // two 16-column chunks per TMEM round trip
+          uint32_t v[2][16];
+          tmem_ld16(treg + 16 * c0, v[0]);
+          if (c0 + 1 < 5) tmem_ld16(treg + 16 * (c0 + 1), v[1]);
+          tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) h[i] = f16x2_bits(v[c][2 * i], v[c][2 * i + 1]);
-            *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(h[4], h[5], h[6], h[7]);
-          } else {
-            uint32_t e[4];
+          for (int u = 0; u < 2; ++u) {
+            const int c = c0 + u;
+            if (c >= 5) break;
+            if (p2f16) {
+              uint32_t h[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              e[i] = e4m3x2_bits(v[c][4 * i], v[c][4 * i + 1]) | (e4m3x2_bits(v[c][4 * i + 2], v[c][4 * i + 3]) << 16);
-            *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
+              for (int i = 0; i < 8; ++i) h[i] = f16x2_bits(v[u][2 * i], v[u][2 * i + 1]);
+              *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(h[0], h[1], h[2], h[3]);
+              *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(h[4], h[5], h[6], h[7]);
+            } else {
+              uint32_t e[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                e[i] = e4m3x2_bits(v[u][4 * i], v[u][4 * i + 1]) | (e4m3x2_bits(v[u][4 * i + 2], v[u][4 * i + 3]) << 16);
+              *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
+            }
           }
         }
       }
@@ -512,19 +505,43 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->h_full);
-
-      // ---- encode the next window while pass 2 runs
+      // encode the next window (pass 1 of tile j, its reader, has completed)
       if (ENC && j + 1 < n_my) {
         const int s1 = (j + 1) % NS;
         const bool ms1 = get_tile<BATCH>(p, first, j + 1).R.C > 2;
         if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
-        encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kWorkerThreads);
+        encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->enc_full);
       }
-
-      // ---- epilogue: S -> next state, staged for the TMA store
+    }
+    if (!ok) set_abort(bars, err0, 8);
+  } else {
+    // ------------------------------------------------ epilogue warps (10 .. 21)
+    // S (D2, lane y, columns x) -> next states, staged for the TMA store.
+    const int etid = threadIdx.x - 64 - kCvtThreads;   // 0 .. kEpiThreads-1
+    const int q = warp & 3;
+    const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..2: which warp of the quarter
+    const int y = 32 * q + lane;                       // TMEM lane = output row y
+    const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
+    const bool store_thread = etid == 0;
+    const int nch = kq < 2 ? 3 : 2;                    // D2 column chunks kq, kq+3, kq+6 (< 8)
+    uint32_t off_ctr[3], off_out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int cc = kq + 3 * c < 8 ? kq + 3 * c : kq;
+      off_ctr[c] = op_off(kWin, 1, y + 16, 16 * cc + 16);
+      off_out[c] = y * 128 + (((cc ^ y) & 7) << 4);
+    }
+    bool ok = true;
+    HalfRule hr = make_half_rule(BATCH ? RuleDev{} : p.rule, kScale);
+    for (int j = 0; ok && j < n_my; ++j) {
+      const int reg = j % kRegions, s = j % NS, o = j & 1;
+      const Tile t = get_tile<BATCH>(p, first, j);
+      const RuleDev &R = t.R;
+      if (BATCH) hr = make_half_rule(R, kScale);
+      const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
       if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       if (store_thread) {
@@ -534,17 +551,17 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p.timeout_ns))) break;
       uint8_t *out = smem + L::kOut + o * L::kOutBytes;
       {
-        // chunks of 16 columns x: warp kq takes kq and kq + 4
-        uint32_t v[2][16];
+        const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
+        uint32_t v[3][16];
         tmem_ld16(treg + 16 * kq, v[0]);
-        tmem_ld16(treg + 16 * (kq + 4), v[1]);
+        tmem_ld16(treg + 16 * (kq + 3), v[1]);
+        if (nch == 3) tmem_ld16(treg + 16 * (kq + 6), v[2]);
         tmem_wait_ld();
-        const int y = row;
         const bool sums_mode = !BATCH && p.sums != nullptr;
         if (!sums_mode && R.C == 2) {
-          const HalfRule hr = make_half_rule(R, kScale);
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
+          for (int c = 0; c < 3; ++c) {
+            if (c >= nch) break;
             const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
             uint4 ov;
             ov.x = rule4_binary(&v[c][0], cv.x, hr);
@@ -555,8 +572,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           }
         } else {
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int cc = kq + 4 * c;
+          for (int c = 0; c < 3; ++c) {
+            if (c >= nch) break;
+            const int cc = kq + 3 * c;
             const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
             const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
             if (sums_mode) {
