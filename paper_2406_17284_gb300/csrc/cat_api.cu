@@ -153,6 +153,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.map_in_a = h->maps[in][0];
     p.map_in_b = h->maps[in][1];
     p.map_out = h->maps[1 - in][2];
+    p.map_ctr = h->maps[in][2];
     p.H = (int32_t)h->H;
     p.W = (int32_t)h->W;
     p.tiles_x = (int32_t)((h->W + 127) / 128);

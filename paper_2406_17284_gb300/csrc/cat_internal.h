@@ -46,6 +46,7 @@ struct TcParams {
   CUtensorMap map_in_a;  // input buffer, box 128 x 160 bytes, 128B swizzle
   CUtensorMap map_in_b;  // input buffer, box  32 x 160 bytes,  32B swizzle
   CUtensorMap map_out;   // output buffer, box 128 x 128 bytes, 128B swizzle
+  CUtensorMap map_ctr;   // input buffer, box 128 x 128 bytes, 128B swizzle (centre tile)
   int32_t H, W, tiles_x, n_tiles;
   RuleDev rule;
   int32_t *err;     // device status word (0 = ok)

@@ -118,9 +118,10 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
     const cat_grid_desc_t &g = grids[i];
     cat::BatchInst &I = h.inst[i];
     memset(&I, 0, sizeof(I));
-    // buffer 0 = g.in (read), buffer 1 = g.out (written): cur = 0, parity 0
+    // buffer 0 = g.in (read, also as centre tiles), buffer 1 = g.out (written): cur = 0, parity 0
     if ((rc = cat::host_make_map(&I.map_in_a[0], (void *)g.in, g.H, g.W, g.pitch, 128, 160, 1))) return rc;
     if ((rc = cat::host_make_map(&I.map_in_b[0], (void *)g.in, g.H, g.W, g.pitch, 32, 160, 0))) return rc;
+    if ((rc = cat::host_make_map(&I.map_out[0], (void *)g.in, g.H, g.W, g.pitch, 128, 128, 1))) return rc;
     if ((rc = cat::host_make_map(&I.map_out[1], g.out, g.H, g.W, g.pitch, 128, 128, 1))) return rc;
     I.rule = cat::host_reduce_rule(g.rule);
     I.H = (int32_t)g.H;

@@ -78,11 +78,16 @@ __device__ __forceinline__ uint64_t op_desc(uint32_t base, int R, int E, int j) 
 }
 
 // DT 0: FP16 kernel; DT 1: FP8 kernel.  ENC: the window is re-encoded in
-// shared memory (always for FP16; for FP8 only when C > 2).
+// shared memory (always for FP16; for FP8 only when C > 2).  The centre tile
+// of every output tile gets its own TMA load into a ring of NR entries that
+// also serves as the output staging (the epilogue overwrites each centre state
+// with the next state in place), so the 160 x 160 window stage is free as
+// soon as pass 1 (or the encoding) has read it.
 template <int DT, bool ENC>
 struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
   static constexpr int NS = (DT == 0 || ENC) ? 2 : 3;         // TMA window stages
+  static constexpr int NR = DT == 0 ? 2 : 3;                  // centre / output ring
   static constexpr uint32_t kBand16 = 0;                      // f16 band
   static constexpr uint32_t kBand16Bytes = kTile * kWin * 2;
   static constexpr uint32_t kBand8 = kBand16 + kBand16Bytes;  // e4m3 band (FP8)
@@ -93,17 +98,18 @@ struct Layout {
   static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E1 : 0;
   static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand
   static constexpr uint32_t kHBytes = kTile * kWin * 2;
-  static constexpr uint32_t kOut = kH + kHBytes;              // output staging x2
-  static constexpr uint32_t kOutBytes = kTile * kTile;
-  static constexpr uint32_t kBars = kOut + 2 * kOutBytes;
+  static constexpr uint32_t kRing = kH + kHBytes;             // centre tiles / output staging
+  static constexpr uint32_t kRingBytes = kTile * kTile;
+  static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
+  static_assert(kDyn <= 232448, "shared memory budget");
 };
 
 struct Bars {
   uint64_t x_full[3], x_empty[3];
+  uint64_t c_full[3], c_empty[3], out_full[3];
   uint64_t d1_full[kRegions], d2_full[kRegions], tmem_empty[kRegions];
   uint64_t h_full, enc_full, band_ready;
-  uint64_t out_free[2], out_full[2];
   uint64_t mma_done, never;
   uint32_t tmem_base;
   int abort;
@@ -231,7 +237,7 @@ __device__ __forceinline__ uint32_t rule4_binary(const uint32_t *v, uint32_t cw,
 
 // What one output tile needs: its maps, origin, grid extent and rule.
 struct Tile {
-  const CUtensorMap *in_a, *in_b, *out;
+  const CUtensorMap *in_a, *in_b, *out, *ctr;
   int x0, y0, H, W;
   RuleDev R;
   int32_t *err;
@@ -262,6 +268,7 @@ __device__ __forceinline__ Tile get_tile(const TcParams &p, int first, int j) {
     t.in_a = &I->map_in_a[in];
     t.in_b = &I->map_in_b[in];
     t.out = &I->map_out[in ^ 1];
+    t.ctr = &I->map_out[in];
     t.x0 = bt.tx * kTile;
     t.y0 = bt.ty * kTile;
     t.H = I->H;
@@ -274,6 +281,7 @@ __device__ __forceinline__ Tile get_tile(const TcParams &p, int first, int j) {
     t.in_a = &p.map_in_a;
     t.in_b = &p.map_in_b;
     t.out = &p.map_out;
+    t.ctr = &p.map_ctr;
     t.x0 = tx * kTile;
     t.y0 = ty * kTile;
     t.H = p.H;
@@ -293,6 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   using L = Layout<DT, ENC>;
   constexpr int E1 = L::E1;
   constexpr int NS = L::NS;
+  constexpr int NR = L::NR;
   constexpr float kScale = DT == 1 ? (1.0f / 512.0f) : 1.0f;   // accumulator = count * kScale
 
   extern __shared__ uint8_t smem_raw[];
@@ -306,7 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) { mbar_init(&bars->x_full[i], 1); mbar_init(&bars->x_empty[i], kEpiWarps); }
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(&bars->x_full[i], 1);
+      mbar_init(&bars->x_empty[i], ENC ? kCvtWarps : 1);  // encoders, or pass 1's commit
+      mbar_init(&bars->c_full[i], 1);
+      mbar_init(&bars->c_empty[i], 1);                    // the store thread
+      mbar_init(&bars->out_full[i], kEpiWarps);
+    }
     for (int i = 0; i < kRegions; ++i) {
       mbar_init(&bars->d1_full[i], 1);
       mbar_init(&bars->d2_full[i], 1);
@@ -315,7 +330,6 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     mbar_init(&bars->h_full, kCvtWarps);
     mbar_init(&bars->enc_full, kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
-    for (int i = 0; i < 2; ++i) { mbar_init(&bars->out_free[i], 1); mbar_init(&bars->out_full[i], kEpiWarps); }
     mbar_init(&bars->mma_done, 1);
     mbar_init(&bars->never, 1);
     bars->abort = 0;
@@ -335,7 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   const uint32_t s_base = smem_u32(smem);
 
   if (warp == 0) {
-    // ---------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------- TMA producers
+    // lane 0 streams the haloed windows (freed by pass 1 or the encoder),
+    // lane 1 the centre tiles (freed once their TMA store has read them).
     if (lane == 0) {
       int issued = 0;
       for (int j = 0; j < n_my; ++j) {
@@ -349,13 +365,28 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         tma_load_2d(xs + kWin * 128, t.in_b, t.x0 + 112, t.y0 - 16, &bars->x_full[s]);
         issued = j + 1;
       }
-      // drain: the last load issued into each stage must have landed
-      volatile int no_abort = 0;
+      volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
       for (int j = issued - 1; j >= 0 && j >= issued - NS; --j)
         if (!mbar_wait(&bars->x_full[j % NS], (j / NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 2);
+    } else if (lane == 1) {
+      int issued = 0;
+      for (int j = 0; j < n_my; ++j) {
+        const int k = j % NR;
+        const Tile t = get_tile<BATCH>(p, first, j);
+        if (j == 0 || BATCH) prefetch_tmap(t.ctr);
+        if (!mbar_wait(&bars->c_empty[k], ((j / NR) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 10); break; }
+        mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
+        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.x0, t.y0, &bars->c_full[k]);
+        issued = j + 1;
+      }
+      volatile int no_abort = 0;
+      for (int j = issued - 1; j >= 0 && j >= issued - NR; --j)
+        if (!mbar_wait(&bars->c_full[j % NR], (j / NR) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 11);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // Issues pass 2 of a tile as soon as its operand is written and pass 1 of
+    // the next tile as soon as its window and accumulator region are free.
     if (lane == 0) {
       const uint32_t idesc1 = idesc_f32acc(128, kWin);
       const uint32_t idesc2 = idesc_f32acc(128, kTile);
@@ -363,63 +394,71 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const uint32_t band16 = s_base + L::kBand16, band8 = s_base + L::kBand8;
       const uint32_t hop = s_base + L::kH;
       bool ok = true;
-      int band_r = r0, prev_r = r0, rebuilds = 0;
+      int band_r = r0, rebuilds = 0;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
         ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
         if (!ok) set_abort(bars, err0, 3);
       }
-      auto pass2 = [&](int jj, int r) -> bool {
-        const int reg = jj % kRegions;
-        if (!mbar_wait(&bars->h_full, jj & 1, &bars->abort, p.timeout_ns)) return false;
-        tc_fence_after();
-        const uint32_t d2 = tmem + reg * kRegionCols;
-        if (pass2_f16(DT, r)) {
-#pragma unroll
-          for (int k = 0; k < 10; ++k)
-            mma_f16(d2, op_desc(band16, kTile, 2, k), op_desc(hop, kTile, 2, k), idesc2, k > 0);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 5; ++k)
-            mma_f8f6f4(d2, op_desc(band8, kTile, 1, k), op_desc(hop, kTile, 1, k), idesc2, k > 0);
-        }
-        mma_commit(&bars->d2_full[reg]);
-        return true;
-      };
-      for (int j = 0; ok && j <= n_my; ++j) {
-        bool p2_done = false;
-        int rj = prev_r;
-        if (j < n_my) rj = get_tile<BATCH>(p, first, j).R.r;
-        if (BATCH && j < n_my && rj != band_r) {
-          // the band changes: finish tile j-1 on the old band, wait for the new one
-          if (j >= 1) {
-            if (!(ok = pass2(j - 1, prev_r))) { set_abort(bars, err0, 5); break; }
-            p2_done = true;
-          }
-          if (!(ok = mbar_wait(&bars->band_ready, rebuilds & 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 9); break; }
-          ++rebuilds;
-          band_r = rj;
-        }
-        if (j < n_my) {  // pass 1 of tile j
-          const int reg = j % kRegions, s = j % NS;
-          ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns);
-          if (ok) ok = ENC ? mbar_wait(&bars->enc_full, j & 1, &bars->abort, p.timeout_ns)
-                           : mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
-          if (!ok) { set_abort(bars, err0, 4); break; }
+      int j1 = 0, j2 = 0;                 // next tile for pass 1 / pass 2
+      int r1 = n_my > 0 ? r0 : 1;          // radius of tile j1
+      bool band_ok = true;                 // band for tile j1 is in place
+      int r_of_p2[kRegions] = {r0, r0, r0};
+      uint64_t t_last = globaltimer_ns();
+      while (ok && j2 < n_my) {
+        bool progress = false;
+        if (j2 < j1 && mbar_try_wait(&bars->h_full, j2 & 1)) {   // pass 2 of tile j2
           tc_fence_after();
-          const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
-          const uint32_t d1 = tmem + reg * kRegionCols;
+          const int reg = j2 % kRegions;
+          const uint32_t d2 = tmem + reg * kRegionCols;
+          if (pass2_f16(DT, r_of_p2[reg])) {
 #pragma unroll
-          for (int k = 0; k < 5 * E1; ++k) {
-            const uint64_t a = op_desc(band1, kTile, E1, k), b = op_desc(win, kWin, E1, k);
-            if constexpr (DT == 0) mma_f16(d1, a, b, idesc1, k > 0);
-            else mma_f8f6f4(d1, a, b, idesc1, k > 0);
+            for (int k = 0; k < 10; ++k)
+              mma_f16(d2, op_desc(band16, kTile, 2, k), op_desc(hop, kTile, 2, k), idesc2, k > 0);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+              mma_f8f6f4(d2, op_desc(band8, kTile, 1, k), op_desc(hop, kTile, 1, k), idesc2, k > 0);
           }
-          mma_commit(&bars->d1_full[reg]);
+          mma_commit(&bars->d2_full[reg]);
+          ++j2;
+          progress = true;
         }
-        if (j >= 1 && !p2_done) {  // pass 2 of tile j - 1
-          if (!(ok = pass2(j - 1, prev_r))) { set_abort(bars, err0, 5); break; }
+        if (j1 < n_my) {                                         // pass 1 of tile j1
+          const int reg = j1 % kRegions, s = j1 % NS;
+          if (!band_ok && j2 == j1 && mbar_try_wait(&bars->band_ready, rebuilds & 1)) {
+            ++rebuilds;
+            band_r = r1;
+            band_ok = true;
+          }
+          if (band_ok && mbar_try_wait(&bars->tmem_empty[reg], ((j1 / kRegions) & 1) ^ 1) &&
+              (ENC ? mbar_try_wait(&bars->enc_full, j1 & 1) : mbar_try_wait(&bars->x_full[s], (j1 / NS) & 1))) {
+            tc_fence_after();
+            const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
+            const uint32_t d1 = tmem + reg * kRegionCols;
+#pragma unroll
+            for (int k = 0; k < 5 * E1; ++k) {
+              const uint64_t a = op_desc(band1, kTile, E1, k), b = op_desc(win, kWin, E1, k);
+              if constexpr (DT == 0) mma_f16(d1, a, b, idesc1, k > 0);
+              else mma_f8f6f4(d1, a, b, idesc1, k > 0);
+            }
+            mma_commit(&bars->d1_full[reg]);
+            if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
+            r_of_p2[reg] = r1;
+            ++j1;
+            progress = true;
+            if (j1 < n_my) {
+              r1 = get_tile<BATCH>(p, first, j1).R.r;
+              band_ok = !BATCH || r1 == band_r;
+            }
+          }
         }
-        prev_r = rj;
+        if (progress) {
+          t_last = globaltimer_ns();
+        } else {
+          if (bars->abort) { ok = false; break; }
+          if (globaltimer_ns() - t_last > p.timeout_ns) { set_abort(bars, err0, 4); ok = false; break; }
+          __nanosleep(32);
+        }
       }
       // drain: every MMA issued above has completed before TMEM is freed
       mma_commit(&bars->mma_done);
@@ -454,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         encode_window<E1>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->enc_full);
+        if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[0]); }
       }
     }
     for (int j = 0; ok && j < n_my; ++j) {
@@ -513,13 +552,14 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->enc_full);
+        if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[s1]); }
       }
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
     // ------------------------------------------------ epilogue warps (10 .. 21)
-    // S (D2, lane y, columns x) -> next states, staged for the TMA store.
+    // S (D2, lane y, columns x) and the centre tile -> next states, written in
+    // place over the centre tile and stored from there by TMA.
     const int etid = threadIdx.x - 64 - kCvtThreads;   // 0 .. kEpiThreads-1
     const int q = warp & 3;
     const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..2: which warp of the quarter
@@ -527,29 +567,27 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
     const bool store_thread = etid == 0;
     const int nch = kq < 2 ? 3 : 2;                    // D2 column chunks kq, kq+3, kq+6 (< 8)
-    uint32_t off_ctr[3], off_out[3];
+    uint32_t off_c[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int cc = kq + 3 * c < 8 ? kq + 3 * c : kq;
-      off_ctr[c] = op_off(kWin, 1, y + 16, 16 * cc + 16);
-      off_out[c] = y * 128 + (((cc ^ y) & 7) << 4);
+      off_c[c] = y * 128 + (((cc ^ y) & 7) << 4);
     }
     bool ok = true;
     HalfRule hr = make_half_rule(BATCH ? RuleDev{} : p.rule, kScale);
     for (int j = 0; ok && j < n_my; ++j) {
-      const int reg = j % kRegions, s = j % NS, o = j & 1;
+      const int reg = j % kRegions, k = j % NR;
       const Tile t = get_tile<BATCH>(p, first, j);
       const RuleDev &R = t.R;
       if (BATCH) hr = make_half_rule(R, kScale);
-      const uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
-      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
-      tc_fence_after();
-      if (store_thread) {
-        bulk_wait_read<1>();  // the store that last read out[o] (tile j-2) is done
-        mbar_arrive(&bars->out_free[o]);
+      if (store_thread && j >= NR - 1) {
+        bulk_wait_read<NR - 2>();   // the store of tile j+1-NR has read its ring entry
+        mbar_arrive(&bars->c_empty[(j + 1) % NR]);
       }
-      if (!(ok = warp_wait(&bars->out_free[o], (j >> 1) & 1, bars, p.timeout_ns))) break;
-      uint8_t *out = smem + L::kOut + o * L::kOutBytes;
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
+      if (!(ok = warp_wait(&bars->c_full[k], (j / NR) & 1, bars, p.timeout_ns))) break;
+      tc_fence_after();
+      uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
       {
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
         uint32_t v[3][16];
@@ -562,20 +600,22 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if (c >= nch) break;
-            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
+            uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
+            const uint4 cv = *cell;
             uint4 ov;
             ov.x = rule4_binary(&v[c][0], cv.x, hr);
             ov.y = rule4_binary(&v[c][4], cv.y, hr);
             ov.z = rule4_binary(&v[c][8], cv.z, hr);
             ov.w = rule4_binary(&v[c][12], cv.w, hr);
-            *reinterpret_cast<uint4 *>(out + off_out[c]) = ov;
+            *cell = ov;
           }
         } else {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if (c >= nch) break;
             const int cc = kq + 3 * c;
-            const uint4 cv = *reinterpret_cast<const uint4 *>(xs + off_ctr[c]);
+            uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
+            const uint4 cv = *cell;
             const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
             if (sums_mode) {
               const int gy = t.y0 + y;
@@ -597,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
                 }
                 ow[i] = word;
               }
-              *reinterpret_cast<uint4 *>(out + off_out[c]) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+              *cell = make_uint4(ow[0], ow[1], ow[2], ow[3]);
             }
           }
         }
@@ -606,14 +646,13 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&bars->out_full[o]);
+        mbar_arrive(&bars->out_full[k]);
         mbar_arrive(&bars->tmem_empty[reg]);
-        mbar_arrive(&bars->x_empty[s]);
       }
       if (store_thread) {
-        if (!mbar_wait(&bars->out_full[o], (j >> 1) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); ok = false; }
+        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); ok = false; }
         else if (BATCH || !p.sums) {
-          tma_store_2d(t.out, t.x0, t.y0, out);
+          tma_store_2d(t.out, t.x0, t.y0, ring);
         }
         bulk_commit();
       }
