@@ -351,7 +351,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   if (warp == 0) {
     // ---------------------------------------------------------- TMA producers
     // lane 0 streams the haloed windows (freed by pass 1 or the encoder),
-    // lane 1 the centre tiles (freed once their TMA store has read them).
+    // lane 1 the centre tiles (freed once their TMA store has read them),
+    // lane 2 stores finished tiles.
     if (lane == 0) {
       int issued = 0;
       for (int j = 0; j < n_my; ++j) {
@@ -382,6 +383,18 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       volatile int no_abort = 0;
       for (int j = issued - 1; j >= 0 && j >= issued - NR; --j)
         if (!mbar_wait(&bars->c_full[j % NR], (j / NR) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 11);
+    } else if (lane == 2) {
+      // store thread: writes each finished tile back and frees its ring entry
+      for (int j = 0; j < n_my; ++j) {
+        const int k = j % NR;
+        const Tile t = get_tile<BATCH>(p, first, j);
+        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
+        if (BATCH || !p.sums) tma_store_2d(t.out, t.x0, t.y0, smem + L::kRing + k * L::kRingBytes);
+        bulk_commit();
+        bulk_wait_read<0>();            // the store has read the entry
+        mbar_arrive(&bars->c_empty[k]);
+      }
+      bulk_wait<0>();                   // all writes complete before the CTA exits
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -423,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           ++j2;
           progress = true;
         }
-        if (j1 < n_my) {                                         // pass 1 of tile j1
+        if (j1 < n_my && j1 <= j2 + 1) {   // pass 1 of tile j1 (never delays a pending pass 2 by more than one pass 1)
           const int reg = j1 % kRegions, s = j1 % NS;
           if (!band_ok && j2 == j1 && mbar_try_wait(&bars->band_ready, rebuilds & 1)) {
             ++rebuilds;
@@ -560,12 +573,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     // ------------------------------------------------ epilogue warps (10 .. 21)
     // S (D2, lane y, columns x) and the centre tile -> next states, written in
     // place over the centre tile and stored from there by TMA.
-    const int etid = threadIdx.x - 64 - kCvtThreads;   // 0 .. kEpiThreads-1
     const int q = warp & 3;
     const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..2: which warp of the quarter
     const int y = 32 * q + lane;                       // TMEM lane = output row y
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
-    const bool store_thread = etid == 0;
     const int nch = kq < 2 ? 3 : 2;                    // D2 column chunks kq, kq+3, kq+6 (< 8)
     uint32_t off_c[3];
 #pragma unroll
@@ -580,10 +591,6 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const Tile t = get_tile<BATCH>(p, first, j);
       const RuleDev &R = t.R;
       if (BATCH) hr = make_half_rule(R, kScale);
-      if (store_thread && j >= NR - 1) {
-        bulk_wait_read<NR - 2>();   // the store of tile j+1-NR has read its ring entry
-        mbar_arrive(&bars->c_empty[(j + 1) % NR]);
-      }
       if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       if (!(ok = warp_wait(&bars->c_full[k], (j / NR) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
@@ -649,17 +656,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         mbar_arrive(&bars->out_full[k]);
         mbar_arrive(&bars->tmem_empty[reg]);
       }
-      if (store_thread) {
-        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); ok = false; }
-        else if (BATCH || !p.sums) {
-          tma_store_2d(t.out, t.x0, t.y0, ring);
-        }
-        bulk_commit();
-      }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     }
     if (!ok) set_abort(bars, err0, 8);
-    if (store_thread) bulk_wait<0>();
   }
 
   tc_fence_before();
