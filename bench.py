@@ -21,6 +21,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -44,6 +46,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=8192,
                     help="rows of the full-width band of the grid the oracle is timed on")
     ap.add_argument("--radii", default="1-16", help="radii to run, e.g. 1-16 or 16 or 1,8,16")
+    ap.add_argument("--batch-count", type=int, default=4096, help="grids in the batched workload (0: skip it)")
     return ap.parse_args()
 
 
@@ -173,6 +176,62 @@ def time_launches(torch, fn, reps, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def measure_batch(args, torch, cat, inputs, stream, steps_per_graph=64):
+    """The heterogeneous batch: `count` grids (sides log-uniform in [64, 2048], r uniform
+    in 1..16, M uniform in {0,1}, p uniform in [0.2, 0.6], the scaled rule, C = 2), 64
+    steps per CUDA-graph launch.  FP8 and FP16 tcgen05 batched launches, and the
+    paper-style FP16 mma.sync kernel launched per grid, on the same states."""
+    from oracle import oracle
+    specs = inputs.batch_instances(args.batch_count, seed=SEED)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(32, os.cpu_count() or 1)) as ex:
+        hosts = list(ex.map(lambda d: inputs.bernoulli(d["H"], d["W"], d["p"], d["seed"]), specs))
+    cells = sum(h.size for h in hosts)
+    grids = [cat.Grid(d["H"], d["W"], d["rule"], kernel="tcgen05", dtype="fp8") for d in specs]
+    for g, h in zip(grids, hosts):
+        cat.cat_set_state(g.handle, h.ctypes.data, h.shape[1], False, stream)
+    stream.synchronize()
+    handles = [g.handle for g in grids]
+    out = {"workload": f"{args.batch_count} grids, sides log-uniform in [64, 2048] (independent H, W), "
+                       "r uniform 1..16, M uniform {0,1}, p uniform [0.2, 0.6], scaled rule C2",
+           "cells": int(cells), "steps_per_launch_graph": steps_per_graph}
+    done = 0
+
+    def timed(fn, reps):
+        evs = time_launches(torch, fn, reps, stream)
+        return statistics.median(evs)
+
+    # FP8 tcgen05, one persistent launch per step, 64 steps per graph
+    cat.cat_batch_step(handles, steps_per_graph, stream)   # plan + graph built, warm-up
+    done += steps_per_graph
+    ms = timed(lambda: cat.cat_batch_step(handles, steps_per_graph, stream), 3)
+    done += 3 * steps_per_graph
+    out["fp8_tcgen05_batched"] = cells * steps_per_graph / (ms / 1000.0)
+    # bit-exactness of the 8 smallest grids after all steps so far
+    small = sorted(range(len(specs)), key=lambda i: hosts[i].size)[:8]
+    stream.synchronize()
+    for i in small:
+        want = oracle.step(hosts[i], oracle.Rule(**specs[i]["rule"]), n_steps=done)
+        if not np.array_equal(grids[i].get_state(stream), want):
+            raise RuntimeError(f"batched grid {i} differs from the oracle")
+    out["oracle_checked_grids"] = len(small)
+    # FP16 tcgen05 batched
+    for g in grids:
+        cat.cat_set_options(g.handle, cat.KERNEL_TCGEN05, cat.DTYPE_FP16)
+    cat.cat_batch_step(handles, steps_per_graph, stream)
+    ms = timed(lambda: cat.cat_batch_step(handles, steps_per_graph, stream), 2)
+    out["fp16_tcgen05_batched"] = cells * steps_per_graph / (ms / 1000.0)
+    # the paper's FP16 fragment scheme, one launch per grid and step
+    for g in grids:
+        cat.cat_set_options(g.handle, cat.KERNEL_MMA_SYNC, cat.DTYPE_FP16)
+    cat.cat_batch_step(handles, 1, stream)
+    ms = timed(lambda: cat.cat_batch_step(handles, 4, stream), 1)
+    out["fp16_paper_mma_sync_per_grid"] = cells * 4 / (ms / 1000.0)
+    for g in grids:
+        g.close()
+    return out
+
+
 def run_cat(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -284,6 +343,10 @@ def run_cat(args, rank, world, local):
                 g.close()
             comps[f"{kern}/{dt}"] = row
 
+    batched = None
+    if args.batch_count > 0 and rank == 0:
+        batched = measure_batch(args, torch, cat, inputs, stream)
+
     cpu = None
     if rank == 0:
         v, dt, cores = oracle_sample(args.cpu_sample, RADII)
@@ -310,6 +373,7 @@ def run_cat(args, rank, world, local):
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": f"ltl_tc_kernel ({args.dtype})"},
             "per_r_cell_updates_per_s": per_r_rate,
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
+            "batched": batched,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,
