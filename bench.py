@@ -111,6 +111,29 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("cat_tc.cu", "ptx.cuh", "cat_internal.h"):
+        with open(os.path.join(ROOT, "paper_2406_17284_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(dtype: str, cells: int):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    scaled to `cells`; None when the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("kernel_source_sha") != kernel_source_sha():
+            return None
+        cap = rec["captures"][dtype]
+        return cap["traffic_bytes_per_launch"] * cells / (rec["grid"][0] * rec["grid"][1])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -369,7 +392,7 @@ def run_cat(args, rank, world, local):
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": args.steps * len(RADII),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": recorded_traffic(args.dtype, n * n),
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": f"ltl_tc_kernel ({args.dtype})"},
             "per_r_cell_updates_per_s": per_r_rate,
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
