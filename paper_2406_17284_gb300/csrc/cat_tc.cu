@@ -21,19 +21,22 @@
 // centre states and writes 16 contiguous next states per access.
 //
 // Precision (exact in every case, Sec. V-A):
-//   FP16 kernel: X, band and H in f16; D1 = H, D2 = S in f32.
+//   FP16 kernel: X, band and H in f16; D1 = H, D2 = S.
 //   FP8 kernel:  pass 1 on e4m3 -- the raw 0/1 state bytes ARE the B operand
 //                (0x01 reads as e4m3 2^-9), so D1 = H * 2^-9 exactly; pass 2
 //                takes H * 2^-9 as e4m3 when 2r+1 <= 15 (all such values are
 //                e4m3 numbers) and as f16 otherwise (e4m3 cannot hold the odd
-//                counts above 16); D2 = S * 2^-9 in f32.
+//                counts above 16); D2 = S * 2^-9.
 // The epilogue compares S (as f16, exact up to 2048) against the rule's
 // ranges two cells at a time in half2 arithmetic.
 //
-// Roles (704 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA
-// issuer, warps 2..9 = convert warps (D1 -> pass-2 operand, window encoding
-// when needed, band rebuilds), warps 10..21 = epilogue warps (fused transition
-// and TMA store).  The two worker roles work on different tiles at once.  Every wait is bounded; on timeout the CTA records
+// Roles (832 threads): warp 0 = TMA loads (lanes 0, 1) and TMA stores (lane 2),
+// warp 1 = TMEM allocator and MMA issuer, warps 2..9 = convert warps (D1 ->
+// pass-2 operand, window encoding when needed, band rebuilds), warps 10..25 =
+// epilogue warps (fused transition).  The two worker roles work on different
+// tiles at once.  Both products accumulate in f16 (exact: every partial sum is
+// a multiple of the operand scale no larger than 1089 times it), so the
+// workers read f16 pairs straight from TMEM.  Every wait is bounded; on timeout the CTA records
 // kDevErrTimeout, drains its own in-flight copies and MMAs, frees TMEM and
 // returns.
 #include <cuda_fp16.h>
@@ -47,7 +50,7 @@ namespace tc {
 constexpr int kTile = 128;
 constexpr int kWin = 160;
 constexpr int kCvtWarps = 8;                       // two per TMEM lane quarter
-constexpr int kEpiWarps = 12;                      // three per TMEM lane quarter
+constexpr int kEpiWarps = 16;                      // four per TMEM lane quarter
 constexpr int kCvtThreads = 32 * kCvtWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kCvtThreads + kEpiThreads;
@@ -183,6 +186,13 @@ __device__ __forceinline__ uint32_t f16x2_bits(uint32_t lo_f32, uint32_t hi_f32)
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Two f16 values (one packed register) -> two e4m3 bytes (low half -> low byte).
+__device__ __forceinline__ uint32_t e4m3x2_from_f16x2(uint32_t h2) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(r) : "r"(h2));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t e4m3x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
   uint16_t r;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(__uint_as_float(hi_f32)), "f"(__uint_as_float(lo_f32)));
@@ -234,6 +244,22 @@ __device__ __forceinline__ uint32_t rule4_binary(const uint32_t *v, uint32_t cw,
                        __hle2_mask(s23, as_h2(__byte_perm(h.bh2, h.sh2, selB)));
   return __byte_perm(m01, m23, 0x6420) & 0x01010101u;
 }
+
+// As rule4_binary, from counts already packed as f16 pairs (cells 0,1 and 2,3).
+// One multiply builds both byte-permute selectors: the low half serves cells
+// 0 and 1, the high half (shifted down) cells 2 and 3.
+__device__ __forceinline__ uint32_t rule4_binary_h(uint32_t s01, uint32_t s23, uint32_t cw, const HalfRule &h) {
+  const uint32_t selA = cw * 0x44u + 0x32103210u;
+  const uint32_t selB = selA >> 16;
+  const uint32_t m01 = __hge2_mask(as_h2(s01), as_h2(__byte_perm(h.bl2, h.sl2, selA))) &
+                       __hle2_mask(as_h2(s01), as_h2(__byte_perm(h.bh2, h.sh2, selA))) & 0x00010001u;
+  const uint32_t m23 = __hge2_mask(as_h2(s23), as_h2(__byte_perm(h.bl2, h.sl2, selB))) &
+                       __hle2_mask(as_h2(s23), as_h2(__byte_perm(h.bh2, h.sh2, selB))) & 0x00010001u;
+  return __byte_perm(m01, m23, 0x6420);
+}
+
+__device__ __forceinline__ float half_lo(uint32_t h2) { return __low2float(as_h2(h2)); }
+__device__ __forceinline__ float half_hi(uint32_t h2) { return __high2float(as_h2(h2)); }
 
 // What one output tile needs: its maps, origin, grid extent and rule.
 struct Tile {
@@ -401,8 +427,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     // Issues pass 2 of a tile as soon as its operand is written and pass 1 of
     // the next tile as soon as its window and accumulator region are free.
     if (lane == 0) {
-      const uint32_t idesc1 = idesc_f32acc(128, kWin);
-      const uint32_t idesc2 = idesc_f32acc(128, kTile);
+      // f16 accumulators: every partial sum is a multiple of the operand scale
+      // up to 1089 * scale, which f16 represents exactly
+      const uint32_t idesc1 = idesc_f16acc(128, kWin);
+      const uint32_t idesc2 = idesc_f16acc(128, kTile);
       const uint32_t band1 = s_base + (DT == 1 ? L::kBand8 : L::kBand16);
       const uint32_t band16 = s_base + L::kBand16, band8 = s_base + L::kBand8;
       const uint32_t hop = s_base + L::kH;
@@ -526,30 +554,24 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       {
+        // D1 is f16 (one value per column); packed loads give f16 pairs, which
+        // are already the pass-2 operand (or become e4m3 pairs with one cvt)
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols + 80 * kq;
+        uint32_t v[5][8];
 #pragma unroll
-        for (int c0 = 0; c0 < 5; c0 += 2) {        // two 16-column chunks per TMEM round trip
-          uint32_t v[2][16];
-          tmem_ld16(treg + 16 * c0, v[0]);
-          if (c0 + 1 < 5) tmem_ld16(treg + 16 * (c0 + 1), v[1]);
-          tmem_wait_ld();
+        for (int c = 0; c < 5; ++c) tmem_ld16_pack16(treg + 16 * c, v[c]);
+        tmem_wait_ld();
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int c = c0 + u;
-            if (c >= 5) break;
-            if (p2f16) {
-              uint32_t h[8];
+        for (int c = 0; c < 5; ++c) {
+          if (p2f16) {
+            *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]);
+            *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(v[c][4], v[c][5], v[c][6], v[c][7]);
+          } else {
+            uint32_t e[4];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) h[i] = f16x2_bits(v[u][2 * i], v[u][2 * i + 1]);
-              *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(h[0], h[1], h[2], h[3]);
-              *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(h[4], h[5], h[6], h[7]);
-            } else {
-              uint32_t e[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                e[i] = e4m3x2_bits(v[u][4 * i], v[u][4 * i + 1]) | (e4m3x2_bits(v[u][4 * i + 2], v[u][4 * i + 3]) << 16);
-              *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
-            }
+            for (int i = 0; i < 4; ++i)
+              e[i] = e4m3x2_from_f16x2(v[c][2 * i]) | (e4m3x2_from_f16x2(v[c][2 * i + 1]) << 16);
+            *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
           }
         }
       }
@@ -570,18 +592,17 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
-    // ------------------------------------------------ epilogue warps (10 .. 21)
+    // ------------------------------------------------ epilogue warps (10 .. 25)
     // S (D2, lane y, columns x) and the centre tile -> next states, written in
     // place over the centre tile and stored from there by TMA.
     const int q = warp & 3;
-    const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..2: which warp of the quarter
+    const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..3: which warp of the quarter
     const int y = 32 * q + lane;                       // TMEM lane = output row y
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
-    const int nch = kq < 2 ? 3 : 2;                    // D2 column chunks kq, kq+3, kq+6 (< 8)
-    uint32_t off_c[3];
+    uint32_t off_c[2];                                 // D2 column chunks kq and kq + 4
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int cc = kq + 3 * c < 8 ? kq + 3 * c : kq;
+    for (int c = 0; c < 2; ++c) {
+      const int cc = kq + 4 * c;
       off_c[c] = y * 128 + (((cc ^ y) & 7) << 4);
     }
     bool ok = true;
@@ -597,40 +618,42 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
       {
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
-        uint32_t v[3][16];
-        tmem_ld16(treg + 16 * kq, v[0]);
-        tmem_ld16(treg + 16 * (kq + 3), v[1]);
-        if (nch == 3) tmem_ld16(treg + 16 * (kq + 6), v[2]);
+        uint32_t v[2][8];                              // S * scale as f16 pairs
+        tmem_ld16_pack16(treg + 16 * kq, v[0]);
+        tmem_ld16_pack16(treg + 16 * (kq + 4), v[1]);
         tmem_wait_ld();
         const bool sums_mode = !BATCH && p.sums != nullptr;
         if (!sums_mode && R.C == 2) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (c >= nch) break;
+          for (int c = 0; c < 2; ++c) {
             uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
             const uint4 cv = *cell;
             uint4 ov;
-            ov.x = rule4_binary(&v[c][0], cv.x, hr);
-            ov.y = rule4_binary(&v[c][4], cv.y, hr);
-            ov.z = rule4_binary(&v[c][8], cv.z, hr);
-            ov.w = rule4_binary(&v[c][12], cv.w, hr);
+            ov.x = rule4_binary_h(v[c][0], v[c][1], cv.x, hr);
+            ov.y = rule4_binary_h(v[c][2], v[c][3], cv.y, hr);
+            ov.z = rule4_binary_h(v[c][4], v[c][5], cv.z, hr);
+            ov.w = rule4_binary_h(v[c][6], v[c][7], cv.w, hr);
             *cell = ov;
           }
         } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (c >= nch) break;
-            const int cc = kq + 3 * c;
+          for (int c = 0; c < 2; ++c) {
+            const int cc = kq + 4 * c;
             uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
             const uint4 cv = *cell;
             const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
+            int cnt[16];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              cnt[2 * i] = __float2int_rn(half_lo(v[c][i]) * (1.0f / kScale));
+              cnt[2 * i + 1] = __float2int_rn(half_hi(v[c][i]) * (1.0f / kScale));
+            }
             if (sums_mode) {
               const int gy = t.y0 + y;
 #pragma unroll
               for (int i = 0; i < 16; ++i) {
                 const int gx = t.x0 + 16 * cc + i;
-                if (gy < t.H && gx < t.W)
-                  p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]) * (1.0f / kScale));
+                if (gy < t.H && gx < t.W) p.sums[(int64_t)gy * p.sums_ld + gx] = cnt[i];
               }
             } else {
               uint32_t ow[4];
@@ -638,10 +661,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
               for (int i = 0; i < 4; ++i) {
                 uint32_t word = 0;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                  const int s_cnt = __float2int_rn(__uint_as_float(v[c][4 * i + b]) * (1.0f / kScale));
-                  word |= next_state(s_cnt, (cw[i] >> (8 * b)) & 0xFFu, R) << (8 * b);
-                }
+                for (int b = 0; b < 4; ++b) word |= next_state(cnt[4 * i + b], (cw[i] >> (8 * b)) & 0xFFu, R) << (8 * b);
                 ow[i] = word;
               }
               *cell = make_uint4(ow[0], ow[1], ow[2], ow[3]);

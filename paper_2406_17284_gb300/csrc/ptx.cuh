@@ -167,6 +167,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "r"(taddr)
       : "memory");
 }
+// Each thread reads 16 consecutive columns of its lane holding 16-bit values
+// (in the low half of each column) and receives them packed two per register:
+// register i = column 2i (low half) | column 2i+1 (high half).
+__device__ __forceinline__ void tmem_ld16_pack16(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.pack::16b.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -189,11 +199,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
 }
 
 // Instruction descriptor for kind::f16 (A, B = F16) and kind::f8f6f4 (A, B =
-// E4M3): both encode format 0 for A and B.  D = F32, both operands K-major.
-//   [4,6) D format (1 = F32), [7,10) A format, [10,13) B format,
+// E4M3): both encode format 0 for A and B; both operands K-major.
+//   [4,6) D format (0 = F16, 1 = F32), [7,10) A format, [10,13) B format,
 //   [15] A major, [16] B major, [17,23) N >> 3, [24,29) M >> 4.
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t M, uint32_t N) {
   return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+// Same with an F16 accumulator (one element in the low half of each TMEM column).
+__host__ __device__ constexpr uint32_t idesc_f16acc(uint32_t M, uint32_t N) {
+  return ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 }  // namespace cat
