@@ -72,12 +72,38 @@ __device__ __forceinline__ uint32_t op_off(int R, int E, int row, int kb) {
   return E * R * 128 + blk * R * 32 + row * 32 + ((((w >> 4) ^ (row >> 2)) & 1) << 4) + (w & 15);
 }
 
-// UMMA descriptor of the 32-byte K-step j of such a tile at shared address base.
-__device__ __forceinline__ uint64_t op_desc(uint32_t base, int R, int E, int j) {
-  const int kb = 32 * j;
-  if (kb < 128 * E) return smem_desc(base + (kb >> 7) * R * 128 + (kb & 127), 16, 1024, kSwizzle128B);
-  const int kk = kb - 128 * E;
-  return smem_desc(base + E * R * 128 + (kk >> 5) * R * 32, 16, 256, kSwizzle32B);
+// UMMA descriptors of such a tile: the 128B-swizzle and 32B-swizzle
+// descriptors of its base address.  K-step j (32 bytes of K) is then the
+// matching one plus a compile-time offset (op_desc_k), so issuing an MMA costs
+// one add per operand instead of a full descriptor encode.
+struct OpDesc {
+  uint64_t d128, d32;
+};
+
+__device__ __forceinline__ OpDesc op_descs(uint32_t base) {
+  return OpDesc{smem_desc(base, 16, 1024, kSwizzle128B), smem_desc(base, 16, 256, kSwizzle32B)};
+}
+
+// The start-address field holds address >> 4 in its low 14 bits; shared
+// addresses stay below 2^18, so adding to it never carries into other fields.
+template <int R, int E, int J>
+__device__ __forceinline__ uint64_t op_desc_k(const OpDesc &d) {
+  constexpr int kb = 32 * J;
+  if constexpr (kb < 128 * E) {
+    return d.d128 + (uint64_t)(((kb >> 7) * R * 128 + (kb & 127)) >> 4);
+  } else {
+    return d.d32 + (uint64_t)((E * R * 128 + ((kb - 128 * E) >> 5) * R * 32) >> 4);
+  }
+}
+
+// Issues the K-steps of one band product: D = A[M=128, K=160] x B[N, K=160]^T.
+template <int KIND, int RA, int RB, int E, int J = 0>
+__device__ __forceinline__ void band_mma(uint32_t d, const OpDesc &a, const OpDesc &b, uint32_t idesc) {
+  if constexpr (J < 5 * E) {
+    if constexpr (KIND == 0) mma_f16(d, op_desc_k<RA, E, J>(a), op_desc_k<RB, E, J>(b), idesc, J > 0);
+    else mma_f8f6f4(d, op_desc_k<RA, E, J>(a), op_desc_k<RB, E, J>(b), idesc, J > 0);
+    band_mma<KIND, RA, RB, E, J + 1>(d, a, b, idesc);
+  }
 }
 
 // DT 0: FP16 kernel; DT 1: FP8 kernel.  ENC: the window is re-encoded in
@@ -431,9 +457,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       // up to 1089 * scale, which f16 represents exactly
       const uint32_t idesc1 = idesc_f16acc(128, kWin);
       const uint32_t idesc2 = idesc_f16acc(128, kTile);
-      const uint32_t band1 = s_base + (DT == 1 ? L::kBand8 : L::kBand16);
-      const uint32_t band16 = s_base + L::kBand16, band8 = s_base + L::kBand8;
-      const uint32_t hop = s_base + L::kH;
+      const OpDesc band1 = op_descs(s_base + (DT == 1 ? L::kBand8 : L::kBand16));
+      const OpDesc band16 = op_descs(s_base + L::kBand16), band8 = op_descs(s_base + L::kBand8);
+      const OpDesc hop = op_descs(s_base + L::kH);
+      const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       int band_r = r0, rebuilds = 0;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -451,15 +478,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           tc_fence_after();
           const int reg = j2 % kRegions;
           const uint32_t d2 = tmem + reg * kRegionCols;
-          if (pass2_f16(DT, r_of_p2[reg])) {
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-              mma_f16(d2, op_desc(band16, kTile, 2, k), op_desc(hop, kTile, 2, k), idesc2, k > 0);
-          } else {
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-              mma_f8f6f4(d2, op_desc(band8, kTile, 1, k), op_desc(hop, kTile, 1, k), idesc2, k > 0);
-          }
+          if (pass2_f16(DT, r_of_p2[reg])) band_mma<0, kTile, kTile, 2>(d2, band16, hop, idesc2);
+          else band_mma<1, kTile, kTile, 1>(d2, band8, hop, idesc2);
           mma_commit(&bars->d2_full[reg]);
           ++j2;
           progress = true;
@@ -474,14 +494,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           if (band_ok && mbar_try_wait(&bars->tmem_empty[reg], ((j1 / kRegions) & 1) ^ 1) &&
               (ENC ? mbar_try_wait(&bars->enc_full, j1 & 1) : mbar_try_wait(&bars->x_full[s], (j1 / NS) & 1))) {
             tc_fence_after();
-            const uint32_t win = ENC ? s_base + L::kXe : s_base + L::kXs + s * L::kXsBytes;
+            const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsBytes) >> 4);   // window stage
+            const OpDesc win{win0.d128 + soff, win0.d32 + soff};
             const uint32_t d1 = tmem + reg * kRegionCols;
-#pragma unroll
-            for (int k = 0; k < 5 * E1; ++k) {
-              const uint64_t a = op_desc(band1, kTile, E1, k), b = op_desc(win, kWin, E1, k);
-              if constexpr (DT == 0) mma_f16(d1, a, b, idesc1, k > 0);
-              else mma_f8f6f4(d1, a, b, idesc1, k > 0);
-            }
+            band_mma<DT == 0 ? 0 : 1, kTile, kWin, E1>(d1, band1, win, idesc1);
             mma_commit(&bars->d1_full[reg]);
             if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
             r_of_p2[reg] = r1;
