@@ -12,6 +12,12 @@
 //   pass 1  D1[x][y'] = sum_x' B[x][x'] X[y'][x']   = H^T   (M=128, N=160, K=160)
 //   pass 2  D2[y][x]  = sum_y' B[y][y'] D1[x][y']   = S     (M=128, N=128, K=160)
 //
+// The band is the A operand of both products and lives in tensor memory
+// (written once per radius by the convert warps); only the window and the
+// pass-2 operand are read from shared memory.  An MMA with both operands in
+// shared memory reads 128 bytes per clock at N = 128, which is all of the
+// SM's shared-memory bandwidth and starves the convert and epilogue warps.
+//
 // The window offset is a fixed 16 cells for every r <= 16, so every TMA load
 // starts on a 16-byte boundary; r only changes the band.  Cells outside the
 // grid arrive as TMA zero fill (dead ghost cells, the zero halo of Sec. IV).
@@ -30,13 +36,16 @@
 // The epilogue compares S (as f16, exact up to 2048) against the rule's
 // ranges two cells at a time in half2 arithmetic.
 //
-// Roles (832 threads): warp 0 = TMA loads (lanes 0, 1) and TMA stores (lane 2),
-// warp 1 = TMEM allocator and MMA issuer, warps 2..9 = convert warps (D1 ->
-// pass-2 operand, window encoding when needed, band rebuilds), warps 10..25 =
-// epilogue warps (fused transition).  The two worker roles work on different
-// tiles at once.  Both products accumulate in f16 (exact: every partial sum is
-// a multiple of the operand scale no larger than 1089 times it), so the
-// workers read f16 pairs straight from TMEM.  Every wait is bounded; on timeout the CTA records
+// Roles (896 threads): warp 0 = window TMA loads, warp 1 = TMEM allocator and
+// pass-1 MMA issuer, warp 2 = centre-tile TMA loads and TMA stores, warp 3 =
+// pass-2 MMA issuer, warps 4..11 = convert warps (D1 -> pass-2 operand,
+// window encoding when needed, bands), warps 12..27 = epilogue warps (fused
+// transition).  The two worker roles
+// work on different tiles at once; tensor memory holds two accumulator
+// regions (D1, then D2, of one tile each) and the bands.  Both products
+// accumulate in f16 (exact: every partial sum is a multiple of the operand
+// scale no larger than 1089 times it), so the workers read f16 pairs straight
+// from TMEM.  Every wait is bounded; on timeout the CTA records
 // kDevErrTimeout, drains its own in-flight copies and MMAs, frees TMEM and
 // returns.
 #include <cuda_fp16.h>
@@ -53,9 +62,11 @@ constexpr int kCvtWarps = 8;                       // two per TMEM lane quarter
 constexpr int kEpiWarps = 16;                      // four per TMEM lane quarter
 constexpr int kCvtThreads = 32 * kCvtWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kThreads = 64 + kCvtThreads + kEpiThreads;
-constexpr int kRegions = 3;
+constexpr int kThreads = 128 + kCvtThreads + kEpiThreads;
+constexpr int kRegions = 2;                        // accumulator regions (D1, then D2 of a tile)
 constexpr int kRegionCols = 160;
+constexpr uint32_t kTmemBand16 = 320;              // f16 band as the A operand: 80 columns
+constexpr uint32_t kTmemBand8 = 416;               // e4m3 band (FP8 kernel): 40 columns
 constexpr uint32_t kTmemCols = 512;
 
 // Byte offset of the element at byte position kb (= k * E) of row `row` in a
@@ -96,13 +107,15 @@ __device__ __forceinline__ uint64_t op_desc_k(const OpDesc &d) {
   }
 }
 
-// Issues the K-steps of one band product: D = A[M=128, K=160] x B[N, K=160]^T.
-template <int KIND, int RA, int RB, int E, int J = 0>
-__device__ __forceinline__ void band_mma(uint32_t d, const OpDesc &a, const OpDesc &b, uint32_t idesc) {
+// Issues the K-steps of one band product: D = A[M=128, K=160] x B[N, K=160]^T
+// with the band A in tensor memory (32 bytes of K = 8 columns per step) and
+// B in shared memory.
+template <int KIND, int RB, int E, int J = 0>
+__device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDesc &b, uint32_t idesc) {
   if constexpr (J < 5 * E) {
-    if constexpr (KIND == 0) mma_f16(d, op_desc_k<RA, E, J>(a), op_desc_k<RB, E, J>(b), idesc, J > 0);
-    else mma_f8f6f4(d, op_desc_k<RA, E, J>(a), op_desc_k<RB, E, J>(b), idesc, J > 0);
-    band_mma<KIND, RA, RB, E, J + 1>(d, a, b, idesc);
+    if constexpr (KIND == 0) mma_f16_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, J > 0);
+    else mma_f8f6f4_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, J > 0);
+    band_mma<KIND, RB, E, J + 1>(d, a_tmem, b, idesc);
   }
 }
 
@@ -117,17 +130,14 @@ struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
   static constexpr int NS = (DT == 0 || ENC) ? 2 : 3;         // TMA window stages
   static constexpr int NR = DT == 0 ? 2 : 3;                  // centre / output ring
-  static constexpr uint32_t kBand16 = 0;                      // f16 band
-  static constexpr uint32_t kBand16Bytes = kTile * kWin * 2;
-  static constexpr uint32_t kBand8 = kBand16 + kBand16Bytes;  // e4m3 band (FP8)
-  static constexpr uint32_t kBand8Bytes = DT == 1 ? kTile * kWin : 0;
-  static constexpr uint32_t kXs = kBand8 + kBand8Bytes;       // u8 windows (TMA)
+  static constexpr int NH = 2;                                // pass-2 operand buffers
+  static constexpr uint32_t kXs = 0;                          // u8 windows (TMA)
   static constexpr uint32_t kXsBytes = kWin * kWin;
   static constexpr uint32_t kXe = kXs + NS * kXsBytes;        // encoded window
   static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E1 : 0;
   static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand
   static constexpr uint32_t kHBytes = kTile * kWin * 2;
-  static constexpr uint32_t kRing = kH + kHBytes;             // centre tiles / output staging
+  static constexpr uint32_t kRing = kH + NH * kHBytes;        // centre tiles / output staging
   static constexpr uint32_t kRingBytes = kTile * kTile;
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
@@ -136,10 +146,10 @@ struct Layout {
 
 struct Bars {
   uint64_t x_full[3], x_empty[3];
-  uint64_t c_full[3], c_empty[3], out_full[3];
+  uint64_t c_full[3], out_full[3];
   uint64_t d1_full[kRegions], d2_full[kRegions], tmem_empty[kRegions];
-  uint64_t h_full, enc_full, band_ready;
-  uint64_t mma_done, never;
+  uint64_t h_full[2], enc_full, band_ready;
+  uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
 };
@@ -185,26 +195,42 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
   }
 }
 
-// Band B[m][k] = one iff k - m in [16 - r, 16 + r]; 128 rows x 10E chunks of 16 bytes.
-template <int E>
-__device__ __forceinline__ void build_band(uint8_t *band, int r, int tid, int nthr) {
-  for (int q = tid; q < kTile * 10 * E; q += nthr) {
-    const int m = q / (10 * E), c = q - m * (10 * E);
-    uint32_t w[4];
+// Band B[m][k] = one iff k - m in [16 - r, 16 + r] as the A operand in tensor
+// memory: row m in lane m, K packed along the columns (two f16 values, or
+// four e4m3 values, per column, the lowest k in the low bits).  The f16 band
+// takes 80 columns, the e4m3 band (FP8 kernel) 40.  Convert warp (q, kq)
+// writes lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
+template <int DT>
+__device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
+  constexpr int kChunks16 = 10, kChunks = DT == 1 ? 15 : 10;
+  const int m = 32 * q + lane;
+  const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
+  for (int c = kq; c < kChunks; c += 2) {          // warp-uniform
+    const bool f16 = c < kChunks16;
+    const int cc = f16 ? c : c - kChunks16;
+    uint32_t v[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t word = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int col = 8 * cc + i;
+      uint32_t w = 0;
+      if (f16) {
 #pragma unroll
-      for (int b = 0; b < 4 / E; ++b) {
-        const int k = (16 * c + 4 * i) / E + b;
-        const int d = k - m;
-        const bool on = d >= 16 - r && d <= 16 + r;
-        word |= on ? (E == 1 ? (0x38u << (8 * b)) : (0x3C00u << (16 * b))) : 0u;
+        for (int b = 0; b < 2; ++b) {
+          const int d = 2 * col + b - m;
+          if (d >= 16 - r && d <= 16 + r) w |= 0x3C00u << (16 * b);
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int d = 4 * col + b - m;
+          if (d >= 16 - r && d <= 16 + r) w |= 0x38u << (8 * b);
+        }
       }
-      w[i] = word;
+      v[i] = w;
     }
-    *reinterpret_cast<uint4 *>(band + op_off(kTile, E, m, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    tmem_st8(tmem + la + (f16 ? kTmemBand16 : kTmemBand8) + 8 * cc, v);
   }
+  tmem_wait_st();
 }
 
 __device__ __forceinline__ uint32_t f16x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
@@ -310,38 +336,71 @@ __device__ __forceinline__ void my_range(const TcParams &p, int &first, int &cou
   }
 }
 
+// Walks this CTA's tiles in order: tile j of the work-list chunk (batch) or
+// tile id blockIdx + j * gridDim (single instance), whose (tx, ty) advances
+// by a fixed step without a division.
 template <bool BATCH>
-__device__ __forceinline__ Tile get_tile(const TcParams &p, int first, int j) {
-  Tile t;
-  if constexpr (BATCH) {
-    const BatchTile bt = p.btiles[first + j];
-    const BatchInst *I = p.binst + bt.inst;
-    const int in = I->cur ^ p.parity;
-    t.in_a = &I->map_in_a[in];
-    t.in_b = &I->map_in_b[in];
-    t.out = &I->map_out[in ^ 1];
-    t.ctr = &I->map_out[in];
-    t.x0 = bt.tx * kTile;
-    t.y0 = bt.ty * kTile;
-    t.H = I->H;
-    t.W = I->W;
-    t.R = I->rule;
-    t.err = I->err;
-  } else {
-    const int id = (int)blockIdx.x + j * (int)gridDim.x;
-    const int ty = id / p.tiles_x, tx = id - ty * p.tiles_x;
-    t.in_a = &p.map_in_a;
-    t.in_b = &p.map_in_b;
-    t.out = &p.map_out;
-    t.ctr = &p.map_ctr;
-    t.x0 = tx * kTile;
-    t.y0 = ty * kTile;
-    t.H = p.H;
-    t.W = p.W;
-    t.R = p.rule;
-    t.err = p.err;
+struct TileSeq {
+  int first, j, tx, ty, sx, sy;
+  __device__ __forceinline__ TileSeq(const TcParams &p, int first_) : first(first_), j(0), tx(0), ty(0), sx(0), sy(0) {
+    if constexpr (!BATCH) {
+      ty = (int)blockIdx.x / p.tiles_x;
+      tx = (int)blockIdx.x - ty * p.tiles_x;
+      sy = (int)gridDim.x / p.tiles_x;
+      sx = (int)gridDim.x - sy * p.tiles_x;
+    }
   }
-  return t;
+  __device__ __forceinline__ void next(const TcParams &p) {
+    ++j;
+    if constexpr (!BATCH) {
+      tx += sx;
+      ty += sy;
+      if (tx >= p.tiles_x) { tx -= p.tiles_x; ++ty; }
+    }
+  }
+  __device__ __forceinline__ Tile get(const TcParams &p) const {
+    Tile t;
+    if constexpr (BATCH) {
+      const BatchTile bt = p.btiles[first + j];
+      const BatchInst *I = p.binst + bt.inst;
+      const int in = I->cur ^ p.parity;
+      t.in_a = &I->map_in_a[in];
+      t.in_b = &I->map_in_b[in];
+      t.out = &I->map_out[in ^ 1];
+      t.ctr = &I->map_out[in];
+      t.x0 = bt.tx * kTile;
+      t.y0 = bt.ty * kTile;
+      t.H = I->H;
+      t.W = I->W;
+      t.R = I->rule;
+      t.err = I->err;
+    } else {
+      t.in_a = &p.map_in_a;
+      t.in_b = &p.map_in_b;
+      t.out = &p.map_out;
+      t.ctr = &p.map_ctr;
+      t.x0 = tx * kTile;
+      t.y0 = ty * kTile;
+      t.H = p.H;
+      t.W = p.W;
+      t.R = p.rule;
+      t.err = p.err;
+    }
+    return t;
+  }
+};
+
+// Rule of tile j of this CTA (the same for every tile of a single instance).
+template <bool BATCH>
+__device__ __forceinline__ RuleDev tile_rule(const TcParams &p, int first, int j) {
+  if constexpr (BATCH) return p.binst[p.btiles[first + j].inst].rule;
+  else return p.rule;
+}
+
+template <bool BATCH>
+__device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j) {
+  if constexpr (BATCH) return p.binst[p.btiles[first + j].inst].err;
+  else return p.err;
 }
 
 // Pass 2 reads f16 in the FP16 kernel and, in the FP8 kernel, whenever H can
@@ -354,6 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   constexpr int E1 = L::E1;
   constexpr int NS = L::NS;
   constexpr int NR = L::NR;
+  constexpr int NH = L::NH;
   constexpr float kScale = DT == 1 ? (1.0f / 512.0f) : 1.0f;   // accumulator = count * kScale
 
   extern __shared__ uint8_t smem_raw[];
@@ -362,8 +422,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int first, n_my;
   my_range<BATCH>(p, first, n_my);
-  int32_t *err0 = BATCH ? (n_my > 0 ? get_tile<BATCH>(p, first, 0).err : nullptr) : p.err;
-  const int r0 = n_my > 0 ? get_tile<BATCH>(p, first, 0).R.r : 1;
+  int32_t *err0 = n_my > 0 ? tile_err<BATCH>(p, first, 0) : (BATCH ? nullptr : p.err);
+  const int r0 = n_my > 0 ? tile_rule<BATCH>(p, first, 0).r : 1;
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
@@ -371,7 +431,6 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       mbar_init(&bars->x_full[i], 1);
       mbar_init(&bars->x_empty[i], ENC ? kCvtWarps : 1);  // encoders, or pass 1's commit
       mbar_init(&bars->c_full[i], 1);
-      mbar_init(&bars->c_empty[i], 1);                    // the store thread
       mbar_init(&bars->out_full[i], kEpiWarps);
     }
     for (int i = 0; i < kRegions; ++i) {
@@ -379,10 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       mbar_init(&bars->d2_full[i], 1);
       mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
-    mbar_init(&bars->h_full, kCvtWarps);
+    mbar_init(&bars->h_full[0], kCvtWarps);
+    mbar_init(&bars->h_full[1], kCvtWarps);
     mbar_init(&bars->enc_full, kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
-    mbar_init(&bars->mma_done, 1);
+    mbar_init(&bars->mma_done[0], 1);
+    mbar_init(&bars->mma_done[1], 1);
     mbar_init(&bars->never, 1);
     bars->abort = 0;
     fence_mbar_init();
@@ -391,8 +452,6 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     tmem_alloc(&bars->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  build_band<2>(smem + L::kBand16, r0, threadIdx.x, kThreads);
-  if (DT == 1) build_band<1>(smem + L::kBand8, r0, threadIdx.x, kThreads);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -401,15 +460,14 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   const uint32_t s_base = smem_u32(smem);
 
   if (warp == 0) {
-    // ---------------------------------------------------------- TMA producers
-    // lane 0 streams the haloed windows (freed by pass 1 or the encoder),
-    // lane 1 the centre tiles (freed once their TMA store has read them),
-    // lane 2 stores finished tiles.
+    // ------------------------------------------------------ window producer
+    // Streams the haloed windows into NS stages (freed by pass 1 or the encoder).
     if (lane == 0) {
       int issued = 0;
-      for (int j = 0; j < n_my; ++j) {
+      TileSeq<BATCH> seq(p, first);
+      for (int j = 0; j < n_my; ++j, seq.next(p)) {
         const int s = j % NS;
-        const Tile t = get_tile<BATCH>(p, first, j);
+        const Tile t = seq.get(p);
         if (j == 0 || BATCH) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
         if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
@@ -421,117 +479,115 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
       for (int j = issued - 1; j >= 0 && j >= issued - NS; --j)
         if (!mbar_wait(&bars->x_full[j % NS], (j / NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 2);
-    } else if (lane == 1) {
-      int issued = 0;
-      for (int j = 0; j < n_my; ++j) {
-        const int k = j % NR;
-        const Tile t = get_tile<BATCH>(p, first, j);
-        if (j == 0 || BATCH) prefetch_tmap(t.ctr);
-        if (!mbar_wait(&bars->c_empty[k], ((j / NR) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 10); break; }
-        mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.x0, t.y0, &bars->c_full[k]);
-        issued = j + 1;
-      }
-      volatile int no_abort = 0;
-      for (int j = issued - 1; j >= 0 && j >= issued - NR; --j)
-        if (!mbar_wait(&bars->c_full[j % NR], (j / NR) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 11);
-    } else if (lane == 2) {
-      // store thread: writes each finished tile back and frees its ring entry
-      for (int j = 0; j < n_my; ++j) {
-        const int k = j % NR;
-        const Tile t = get_tile<BATCH>(p, first, j);
-        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
-        if (BATCH || !p.sums) tma_store_2d(t.out, t.x0, t.y0, smem + L::kRing + k * L::kRingBytes);
-        bulk_commit();
-        bulk_wait_read<0>();            // the store has read the entry
-        mbar_arrive(&bars->c_empty[k]);
-      }
-      bulk_wait<0>();                   // all writes complete before the CTA exits
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    // Issues pass 2 of a tile as soon as its operand is written and pass 1 of
-    // the next tile as soon as its window and accumulator region are free.
+    // ---------------------------------------------------- pass-1 MMA issuer
+    // D1 of tile j into region j % 2 once the epilogue has read that region's
+    // previous D2, the window is in place and the bands match the radius.
+    // Each issuer blocks on exactly the barrier it needs next, so neither
+    // polls; the two passes are issued from different warps.
     if (lane == 0) {
       // f16 accumulators: every partial sum is a multiple of the operand scale
       // up to 1089 * scale, which f16 represents exactly
       const uint32_t idesc1 = idesc_f16acc(128, kWin);
-      const uint32_t idesc2 = idesc_f16acc(128, kTile);
-      const OpDesc band1 = op_descs(s_base + (DT == 1 ? L::kBand8 : L::kBand16));
-      const OpDesc band16 = op_descs(s_base + L::kBand16), band8 = op_descs(s_base + L::kBand8);
-      const OpDesc hop = op_descs(s_base + L::kH);
+      const uint32_t band1 = tmem + (DT == 1 ? kTmemBand8 : kTmemBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
-      int band_r = r0, rebuilds = 0;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
         ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
         if (!ok) set_abort(bars, err0, 3);
       }
-      int j1 = 0, j2 = 0;                 // next tile for pass 1 / pass 2
-      int r1 = n_my > 0 ? r0 : 1;          // radius of tile j1
-      bool band_ok = true;                 // band for tile j1 is in place
-      int r_of_p2[kRegions] = {r0, r0, r0};
-      uint64_t t_last = globaltimer_ns();
-      while (ok && j2 < n_my) {
-        bool progress = false;
-        if (j2 < j1 && mbar_try_wait(&bars->h_full, j2 & 1)) {   // pass 2 of tile j2
-          tc_fence_after();
-          const int reg = j2 % kRegions;
-          const uint32_t d2 = tmem + reg * kRegionCols;
-          if (pass2_f16(DT, r_of_p2[reg])) band_mma<0, kTile, kTile, 2>(d2, band16, hop, idesc2);
-          else band_mma<1, kTile, kTile, 1>(d2, band8, hop, idesc2);
-          mma_commit(&bars->d2_full[reg]);
-          ++j2;
-          progress = true;
+      int band_r = -1, builds = 0;
+      for (int j = 0; ok && j < n_my; ++j) {
+        const int reg = j % kRegions, s = j % NS;
+        const int r = tile_rule<BATCH>(p, first, j).r;
+        if (r != band_r) {                 // the convert warps have built the bands for r
+          if (!(ok = mbar_wait(&bars->band_ready, builds & 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 4); break; }
+          ++builds;
+          band_r = r;
         }
-        if (j1 < n_my && j1 <= j2 + 1) {   // pass 1 of tile j1 (never delays a pending pass 2 by more than one pass 1)
-          const int reg = j1 % kRegions, s = j1 % NS;
-          if (!band_ok && j2 == j1 && mbar_try_wait(&bars->band_ready, rebuilds & 1)) {
-            ++rebuilds;
-            band_r = r1;
-            band_ok = true;
-          }
-          if (band_ok && mbar_try_wait(&bars->tmem_empty[reg], ((j1 / kRegions) & 1) ^ 1) &&
-              (ENC ? mbar_try_wait(&bars->enc_full, j1 & 1) : mbar_try_wait(&bars->x_full[s], (j1 / NS) & 1))) {
-            tc_fence_after();
-            const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsBytes) >> 4);   // window stage
-            const OpDesc win{win0.d128 + soff, win0.d32 + soff};
-            const uint32_t d1 = tmem + reg * kRegionCols;
-            band_mma<DT == 0 ? 0 : 1, kTile, kWin, E1>(d1, band1, win, idesc1);
-            mma_commit(&bars->d1_full[reg]);
-            if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
-            r_of_p2[reg] = r1;
-            ++j1;
-            progress = true;
-            if (j1 < n_my) {
-              r1 = get_tile<BATCH>(p, first, j1).R.r;
-              band_ok = !BATCH || r1 == band_r;
-            }
-          }
-        }
-        if (progress) {
-          t_last = globaltimer_ns();
-        } else {
-          if (bars->abort) { ok = false; break; }
-          if (globaltimer_ns() - t_last > p.timeout_ns) { set_abort(bars, err0, 4); ok = false; break; }
-          __nanosleep(32);
-        }
+        if (!(ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 5); break; }
+        if (ENC) ok = mbar_wait(&bars->enc_full, j & 1, &bars->abort, p.timeout_ns);
+        else ok = mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
+        if (!ok) { set_abort(bars, err0, 6); break; }
+        tc_fence_after();
+        const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsBytes) >> 4);   // window stage
+        const OpDesc win{win0.d128 + soff, win0.d32 + soff};
+        band_mma<DT == 0 ? 0 : 1, kWin, E1>(tmem + reg * kRegionCols, band1, win, idesc1);
+        mma_commit(&bars->d1_full[reg]);
+        if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
       }
       // drain: every MMA issued above has completed before TMEM is freed
-      mma_commit(&bars->mma_done);
+      mma_commit(&bars->mma_done[0]);
       volatile int no_abort = 0;
-      if (!mbar_wait(&bars->mma_done, 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 6);
+      if (!mbar_wait(&bars->mma_done[0], 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 12);
     }
-  } else if (warp < 2 + kCvtWarps) {
-    // ------------------------------------------------- convert warps (2 .. 9)
+  } else if (warp == 2) {
+    // ------------------------------------------------ centre tiles and stores
+    // One thread: loads the centre tiles into the ring, stores each finished
+    // tile from its entry and reloads the entry with the centre tile NR ahead
+    // once the store has read it.  (Kept out of warp 0: a lane suspended in a
+    // barrier wait holds up the other lanes of its warp.)
+    if (lane == 0) {
+      int issued = 0;
+      TileSeq<BATCH> lseq(p, first), sseq(p, first);
+      auto load_ctr = [&](int j) {
+        const int k = j % NR;
+        const Tile t = lseq.get(p);
+        if (j == 0 || BATCH) prefetch_tmap(t.ctr);
+        mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
+        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.x0, t.y0, &bars->c_full[k]);
+        lseq.next(p);
+        issued = j + 1;
+      };
+      for (int j = 0; j < n_my && j < NR; ++j) load_ctr(j);
+      for (int j = 0; j < n_my; ++j, sseq.next(p)) {
+        const int k = j % NR;
+        const Tile t = sseq.get(p);
+        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
+        if (BATCH || !p.sums) {
+          tma_store_2d(t.out, t.x0, t.y0, smem + L::kRing + k * L::kRingBytes);
+          bulk_commit();
+          bulk_wait_read<0>();          // the store has read the entry
+        }
+        if (j + NR < n_my) load_ctr(j + NR);
+      }
+      bulk_wait<0>();                   // all writes complete before the CTA exits
+      volatile int no_abort = 0;        // drain: the last load issued into each entry has landed
+      for (int j = issued - 1; j >= 0 && j >= issued - NR; --j)
+        if (!mbar_wait(&bars->c_full[j % NR], (j / NR) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 11);
+    }
+  } else if (warp == 3) {
+    // ---------------------------------------------------- pass-2 MMA issuer
+    // D2 of tile j over its D1 region once the convert warps have written H.
+    if (lane == 0) {
+      const uint32_t idesc2 = idesc_f16acc(128, kTile);
+      const uint32_t band16 = tmem + kTmemBand16, band8 = tmem + kTmemBand8;
+      const OpDesc hop0 = op_descs(s_base + L::kH);
+      for (int j = 0; j < n_my; ++j) {
+        if (!mbar_wait(&bars->h_full[j % NH], (j / NH) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, err0, 9); break; }
+        tc_fence_after();
+        const int reg = j % kRegions;
+        const uint64_t hoff = (uint64_t)(((j % NH) * L::kHBytes) >> 4);
+        const OpDesc hop{hop0.d128 + hoff, hop0.d32 + hoff};
+        const uint32_t d2 = tmem + reg * kRegionCols;
+        if (pass2_f16(DT, tile_rule<BATCH>(p, first, j).r)) band_mma<0, kTile, 2>(d2, band16, hop, idesc2);
+        else band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
+        mma_commit(&bars->d2_full[reg]);
+      }
+      mma_commit(&bars->mma_done[1]);
+      volatile int no_abort = 0;
+      if (!mbar_wait(&bars->mma_done[1], 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 13);
+    }
+  } else if (warp < 4 + kCvtWarps) {
+    // ------------------------------------------------ convert warps (4 .. 11)
     // D1 (H^T, lane x, columns y') -> K-major pass-2 operand; window encoding
     // for the next tile; band rebuilds when the radius changes (batch mode).
-    const int wtid = threadIdx.x - 64;            // 0 .. kCvtThreads-1
+    const int wtid = threadIdx.x - 128;           // 0 .. kCvtThreads-1
     const int q = warp & 3;                       // TMEM lane quarter of this warp
-    const int kq = (warp - 2) >> 2;               // 0..1: which warp of the quarter
+    const int kq = (warp - 4) >> 2;               // 0..1: which warp of the quarter
     const int row = 32 * q + lane;                // TMEM lane = x
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
-    uint8_t *hop = smem + L::kH;
     bool ok = true;
     int band_r = r0;
     // this thread's operand offsets: D1 column chunks 5kq .. 5kq+4 (16 columns each)
@@ -543,11 +599,15 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       off16b[c] = op_off(kTile, 2, row, 32 * cc + 16);
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
+    // the bands for the first tile
+    store_bands<DT>(tmem, r0, q, kq, lane);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars->band_ready);
     if (ENC && n_my > 0) {
-      const Tile t0 = get_tile<BATCH>(p, first, 0);
       ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
       if (ok) {
-        encode_window<E1>(smem + L::kXs, smem + L::kXe, t0.R.C > 2, wtid, kCvtThreads);
+        encode_window<E1>(smem + L::kXs, smem + L::kXe, tile_rule<BATCH>(p, first, 0).C > 2, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[0]); }
@@ -555,17 +615,19 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     for (int j = 0; ok && j < n_my; ++j) {
       const int reg = j % kRegions;
-      const Tile t = get_tile<BATCH>(p, first, j);
-      const bool p2f16 = pass2_f16(DT, t.R.r);
-      // pass 2 of tile j-1 has finished reading H (and, if the radius changes, the bands)
-      if (j >= 1 && !(ok = warp_wait(&bars->d2_full[(j - 1) % kRegions], ((j - 1) / kRegions) & 1, bars, p.timeout_ns))) break;
-      if (BATCH && t.R.r != band_r) {
-        build_band<2>(smem + L::kBand16, t.R.r, wtid, kCvtThreads);
-        if (DT == 1) build_band<1>(smem + L::kBand8, t.R.r, wtid, kCvtThreads);
-        fence_proxy_async_smem();
+      const int rj = tile_rule<BATCH>(p, first, j).r;
+      const bool p2f16 = pass2_f16(DT, rj);
+      // pass 2 of tile j-NH has finished reading this H buffer
+      if (j >= NH && !(ok = warp_wait(&bars->d2_full[(j - NH) % kRegions], ((j - NH) / kRegions) & 1, bars, p.timeout_ns))) break;
+      if (BATCH && rj != band_r) {
+        // every pass 2 so far (tile j-1 last) has finished reading the bands
+        if (NH > 1 && j >= 1 && !(ok = warp_wait(&bars->d2_full[(j - 1) % kRegions], ((j - 1) / kRegions) & 1, bars, p.timeout_ns))) break;
+        tc_fence_after();
+        store_bands<DT>(tmem, rj, q, kq, lane);
+        tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
-        band_r = t.R.r;
+        band_r = rj;
       }
       if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
@@ -573,6 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         // D1 is f16 (one value per column); packed loads give f16 pairs, which
         // are already the pass-2 operand (or become e4m3 pairs with one cvt)
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols + 80 * kq;
+        uint8_t *hop = smem + L::kH + (j % NH) * L::kHBytes;
         uint32_t v[5][8];
 #pragma unroll
         for (int c = 0; c < 5; ++c) tmem_ld16_pack16(treg + 16 * c, v[c]);
@@ -594,11 +657,11 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       fence_proxy_async_smem();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->h_full);
+      if (lane == 0) mbar_arrive(&bars->h_full[j % NH]);
       // encode the next window (pass 1 of tile j, its reader, has completed)
       if (ENC && j + 1 < n_my) {
         const int s1 = (j + 1) % NS;
-        const bool ms1 = get_tile<BATCH>(p, first, j + 1).R.C > 2;
+        const bool ms1 = tile_rule<BATCH>(p, first, j + 1).C > 2;
         if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
         encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kCvtThreads);
         fence_proxy_async_smem();
@@ -608,11 +671,11 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
-    // ------------------------------------------------ epilogue warps (10 .. 25)
+    // ------------------------------------------------ epilogue warps (12 .. 27)
     // S (D2, lane y, columns x) and the centre tile -> next states, written in
     // place over the centre tile and stored from there by TMA.
     const int q = warp & 3;
-    const int kq = (warp - 2 - kCvtWarps) >> 2;        // 0..3: which warp of the quarter
+    const int kq = (warp - 4 - kCvtWarps) >> 2;        // 0..3: which warp of the quarter
     const int y = 32 * q + lane;                       // TMEM lane = output row y
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
     uint32_t off_c[2];                                 // D2 column chunks kq and kq + 4
@@ -623,9 +686,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     }
     bool ok = true;
     HalfRule hr = make_half_rule(BATCH ? RuleDev{} : p.rule, kScale);
-    for (int j = 0; ok && j < n_my; ++j) {
+    TileSeq<BATCH> seq(p, first);
+    for (int j = 0; ok && j < n_my; ++j, seq.next(p)) {
       const int reg = j % kRegions, k = j % NR;
-      const Tile t = get_tile<BATCH>(p, first, j);
+      const Tile t = seq.get(p);
       const RuleDev &R = t.R;
       if (BATCH) hr = make_half_rule(R, kScale);
       if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
@@ -638,6 +702,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         tmem_ld16_pack16(treg + 16 * kq, v[0]);
         tmem_ld16_pack16(treg + 16 * (kq + 4), v[1]);
         tmem_wait_ld();
+        tc_fence_before();             // this tile's region may take the next pass 1
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->tmem_empty[reg]);
         const bool sums_mode = !BATCH && p.sums != nullptr;
         if (!sums_mode && R.C == 2) {
 #pragma unroll
@@ -686,12 +753,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         }
       }
       fence_proxy_async_smem();
-      tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&bars->out_full[k]);
-        mbar_arrive(&bars->tmem_empty[reg]);
-      }
+      if (lane == 0) mbar_arrive(&bars->out_full[k]);
     }
     if (!ok) set_abort(bars, err0, 8);
   }
