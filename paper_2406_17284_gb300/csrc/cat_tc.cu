@@ -233,24 +233,6 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
   tmem_wait_st();
 }
 
-__device__ __forceinline__ uint32_t f16x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
-  __half2 h = __floats2half2_rn(__uint_as_float(lo_f32), __uint_as_float(hi_f32));
-  return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// Two f16 values (one packed register) -> two e4m3 bytes (low half -> low byte).
-__device__ __forceinline__ uint32_t e4m3x2_from_f16x2(uint32_t h2) {
-  uint16_t r;
-  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(r) : "r"(h2));
-  return r;
-}
-
-__device__ __forceinline__ uint32_t e4m3x2_bits(uint32_t lo_f32, uint32_t hi_f32) {
-  uint16_t r;
-  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(__uint_as_float(hi_f32)), "f"(__uint_as_float(lo_f32)));
-  return r;
-}
-
 // Next state of one cell from its box count s and state c (see RuleDev).
 __device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev &R) {
   if (c == 0) return (uint32_t)(s - R.b_lo) <= (uint32_t)R.b_w;
@@ -283,31 +265,27 @@ __device__ __forceinline__ HalfRule make_half_rule(const RuleDev &R, float scale
 
 __device__ __forceinline__ __half2 as_h2(uint32_t v) { return *reinterpret_cast<const __half2 *>(&v); }
 
-// 4 next states (C == 2) from 4 accumulator values and 4 centre bytes (0/1).
-// The centre bits pick each cell's bounds with one byte permute: selector
-// nibbles 0..3 take the birth pair, 4..7 the survival pair.
-__device__ __forceinline__ uint32_t rule4_binary(const uint32_t *v, uint32_t cw, const HalfRule &h) {
-  const uint32_t selA = cw * 0x44u + 0x3210u;          // cells 0, 1 (low 16 bits used)
-  const uint32_t selB = (cw >> 16) * 0x44u + 0x3210u;  // cells 2, 3
-  const __half2 s01 = as_h2(f16x2_bits(v[0], v[1])), s23 = as_h2(f16x2_bits(v[2], v[3]));
-  const uint32_t m01 = __hge2_mask(s01, as_h2(__byte_perm(h.bl2, h.sl2, selA))) &
-                       __hle2_mask(s01, as_h2(__byte_perm(h.bh2, h.sh2, selA)));
-  const uint32_t m23 = __hge2_mask(s23, as_h2(__byte_perm(h.bl2, h.sl2, selB))) &
-                       __hle2_mask(s23, as_h2(__byte_perm(h.bh2, h.sh2, selB)));
-  return __byte_perm(m01, m23, 0x6420) & 0x01010101u;
-}
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
 // As rule4_binary, from counts already packed as f16 pairs (cells 0,1 and 2,3).
-// One multiply builds both byte-permute selectors: the low half serves cells
-// 0 and 1, the high half (shifted down) cells 2 and 3.
+// One multiply builds both byte-permute selectors (low half: cells 0, 1; high
+// half shifted down: cells 2, 3).  A cell is in range iff (s - lo)(hi - s) is
+// not negative: for lo <= hi both factors are exact multiples of the scale and
+// every nonzero product is at least scale^2 >= 2^-18, so no sign is lost to
+// underflow (an overflow to infinity keeps its sign); an empty range has
+// lo = 4096 * scale > s and hi = 2048 * scale > s, so its product is negative.
+// The subtractions and products run on the FMA pipe, and one byte permute
+// replicates each product's sign bit over its cell's byte.
 __device__ __forceinline__ uint32_t rule4_binary_h(uint32_t s01, uint32_t s23, uint32_t cw, const HalfRule &h) {
   const uint32_t selA = cw * 0x44u + 0x32103210u;
   const uint32_t selB = selA >> 16;
-  const uint32_t m01 = __hge2_mask(as_h2(s01), as_h2(__byte_perm(h.bl2, h.sl2, selA))) &
-                       __hle2_mask(as_h2(s01), as_h2(__byte_perm(h.bh2, h.sh2, selA))) & 0x00010001u;
-  const uint32_t m23 = __hge2_mask(as_h2(s23), as_h2(__byte_perm(h.bl2, h.sl2, selB))) &
-                       __hle2_mask(as_h2(s23), as_h2(__byte_perm(h.bh2, h.sh2, selB))) & 0x00010001u;
-  return __byte_perm(m01, m23, 0x6420);
+  const __half2 t01 = __hmul2(__hsub2(as_h2(s01), as_h2(__byte_perm(h.bl2, h.sl2, selA))),
+                              __hsub2(as_h2(__byte_perm(h.bh2, h.sh2, selA)), as_h2(s01)));
+  const __half2 t23 = __hmul2(__hsub2(as_h2(s23), as_h2(__byte_perm(h.bl2, h.sl2, selB))),
+                              __hsub2(as_h2(__byte_perm(h.bh2, h.sh2, selB)), as_h2(s23)));
+  uint32_t neg;   // bytes 1, 3 of t01 and 5, 7 of t23 (the sign bytes), sign-replicated
+  asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(neg) : "r"(h2_bits(t01)), "r"(h2_bits(t23)));
+  return ~neg & 0x01010101u;
 }
 
 __device__ __forceinline__ float half_lo(uint32_t h2) { return __low2float(as_h2(h2)); }
@@ -646,10 +624,14 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
             *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]);
             *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(v[c][4], v[c][5], v[c][6], v[c][7]);
           } else {
+            // the e4m3 code of k * 2^-9 is k itself for k <= 15, and k * 2^-9 *
+            // 512 + 1024 is exactly 1024 + k, an f16 whose low byte is k
+            const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
             uint32_t e[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              e[i] = e4m3x2_from_f16x2(v[c][2 * i]) | (e4m3x2_from_f16x2(v[c][2 * i + 1]) << 16);
+              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k512, k1024)),
+                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k512, k1024)), 0x6420);
             *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
           }
         }
@@ -693,18 +675,22 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       const RuleDev &R = t.R;
       if (BATCH) hr = make_half_rule(R, kScale);
       if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
-      if (!(ok = warp_wait(&bars->c_full[k], (j / NR) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
-      uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
+      // read S and free the region (the next pass 1 waits for it) before
+      // waiting for the centre tile
+      uint32_t v[2][8];                                // S * scale as f16 pairs
       {
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
-        uint32_t v[2][8];                              // S * scale as f16 pairs
         tmem_ld16_pack16(treg + 16 * kq, v[0]);
         tmem_ld16_pack16(treg + 16 * (kq + 4), v[1]);
         tmem_wait_ld();
-        tc_fence_before();             // this tile's region may take the next pass 1
+        tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->tmem_empty[reg]);
+      }
+      if (!(ok = warp_wait(&bars->c_full[k], (j / NR) & 1, bars, p.timeout_ns))) break;
+      uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
+      {
         const bool sums_mode = !BATCH && p.sums != nullptr;
         if (!sums_mode && R.C == 2) {
 #pragma unroll
