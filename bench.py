@@ -47,6 +47,7 @@ def parse():
                     help="rows of the full-width band of the grid the oracle is timed on")
     ap.add_argument("--radii", default="1-16", help="radii to run, e.g. 1-16 or 16 or 1,8,16")
     ap.add_argument("--batch-count", type=int, default=4096, help="grids in the batched workload (0: skip it)")
+    ap.add_argument("--multistate-size", type=int, default=49152, help="side of the multi-state grid (0: skip it)")
     return ap.parse_args()
 
 
@@ -255,6 +256,32 @@ def measure_batch(args, torch, cat, inputs, stream, steps_per_graph=64):
     return out
 
 
+def measure_multistate(args, torch, cat, inputs, stream):
+    """The multi-state workload: a 49152^2 grid with states uniform over {0..15} under
+    R10 C16 M1 S150..260 B150..200 (FP8 operands, window re-encoded so only state 1
+    counts), timed over its first steps while it still holds decaying cells, and a
+    batch of 256 such grids of 2048^2."""
+    rule = inputs.MULTISTATE_R10_C16
+    n = args.multistate_size
+    out = {"workload": f"{n}x{n} and 256 x 2048x2048, states uniform over 0..15, R10 C16 M1 S150..260 B150..200"}
+    g = cat.Grid(n, n, rule, kernel="tcgen05", dtype="fp8")
+    g.set_state(inputs.uniform_states(n, n, 16, 4915))
+    g.step(1, stream)
+    t = time_launches(torch, lambda: g.step(1, stream), 4, stream)
+    out["single_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
+    g.close()
+    grids = [cat.Grid(2048, 2048, rule, kernel="tcgen05", dtype="fp8") for _ in range(256)]
+    for i, gg in enumerate(grids):
+        gg.set_state(inputs.uniform_states(2048, 2048, 16, 5000 + i))
+    handles = [gg.handle for gg in grids]
+    cat.cat_batch_step(handles, 4, stream)                  # plan + graph built
+    ms = statistics.median(time_launches(torch, lambda: cat.cat_batch_step(handles, 4, stream), 3, stream))
+    out["batch_256x2048_cell_updates_per_s"] = 256 * 2048 * 2048 * 4 / (ms / 1000.0)
+    for gg in grids:
+        gg.close()
+    return out
+
+
 def run_cat(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -369,6 +396,9 @@ def run_cat(args, rank, world, local):
     batched = None
     if args.batch_count > 0 and rank == 0:
         batched = measure_batch(args, torch, cat, inputs, stream)
+    multistate = None
+    if args.multistate_size > 0 and rank == 0:
+        multistate = measure_multistate(args, torch, cat, inputs, stream)
 
     cpu = None
     if rank == 0:
@@ -397,6 +427,7 @@ def run_cat(args, rank, world, local):
             "per_r_cell_updates_per_s": per_r_rate,
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
             "batched": batched,
+            "multistate": multistate,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,

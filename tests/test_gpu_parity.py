@@ -253,6 +253,45 @@ def test_cross_dtype_equality_after_many_steps(cat):
         assert_same(ref, want, f"r={r} oracle")
 
 
+def test_multistate_r10_c16_49152_thousand_steps(cat):
+    """The multi-state workload at full size: 49152^2, states uniform over
+    {0..15}, R10 C16 M1 S150..260 B150..200, FP8 operands (re-encoded window).
+    One step is checked against the oracle on 6 windows after steps 1, 2 and 7;
+    with ~1/16 of the cells alive (counts ~28 << 150) nothing is born and every
+    live cell decays, so the grid is all dead by step 16 and stays dead through
+    step 1000."""
+    N, C = 49152, 16
+    rule = inputs.MULTISTATE_R10_C16
+    g = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8")
+    rng = np.random.default_rng(49152)
+    try:
+        g.set_state(inputs.uniform_states(N, N, C, 4915))
+        done = 0
+        for check_at in (1, 2, 7):
+            g.step(check_at - 1 - done)
+            pos = [tuple(int(v) for v in rng.integers(0, N - 128, 2)) for _ in range(6)]
+            pos[0] = (0, N - 128)                       # a corner tile with zero halo on two sides
+            st = g.state_tensor()
+            befores = []
+            for y0, x0 in pos:
+                ya, xa = max(0, y0 - 10), max(0, x0 - 10)
+                befores.append((ya, xa, st[ya:min(N, y0 + 138), xa:min(N, x0 + 138)].cpu().numpy()))
+            g.step(1)
+            done = check_at
+            assert g.status() == cat.CAT_OK
+            st = g.state_tensor()
+            for (y0, x0), (ya, xa, win) in zip(pos, befores):
+                want = oracle.step(win, orule(rule))[y0 - ya:y0 - ya + 128, x0 - xa:x0 - xa + 128]
+                assert_same(st[y0:y0 + 128, x0:x0 + 128].cpu().numpy(), want, f"step {check_at} window ({y0},{x0})")
+        g.step(16 - done)
+        assert not bool(g.state_tensor().any().item())
+        g.step(1000 - 16)
+        assert g.status() == cat.CAT_OK
+        assert not bool(g.state_tensor().any().item())
+    finally:
+        g.close()
+
+
 def test_multistate_r10_c16_windows(cat):
     """R10 C16 M1 S150..260 B150..200 from states uniform over {0..15}, 4096^2.
     One step is checked on 8 windows against the oracle at steps 1, 2, 7 and 14.
