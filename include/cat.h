@@ -99,10 +99,15 @@ typedef struct cat_instance *cat_handle_t;
 
 /* Creates an instance: validates the rule and the shape, allocates two
  * pitch-padded device buffers (ping-pong, Sec. IV-C; pitch = W rounded up to a
- * multiple of 16 bytes) and builds the TMA descriptors.  The state is all zero
- * until cat_set_state.  The instance owns its buffers; cat_destroy frees them.
- * Uses the current CUDA device.  Errors: INVALID_ARG (H or W < 1, H*W > 2^40,
- * bad rule), UNSUPPORTED (periodic boundary, nbhd != 'M'), OOM, CUDA.        */
+ * multiple of 16 bytes) and builds the TMA descriptors.  boundary:
+ * CAT_BOUNDARY_ZERO (cells outside the grid are dead) or CAT_BOUNDARY_PERIODIC
+ * (the grid wraps around in both directions, the paper's setting, Sec. V); a
+ * periodic grid sits inside a 16-cell ghost frame (pitch = W + 32 rounded up to
+ * 16), refreshed by a small kernel before every step, and is stepped by the
+ * tcgen05 kernel only.  The state is all zero until cat_set_state.  The
+ * instance owns its buffers; cat_destroy frees them.  Uses the current CUDA
+ * device.  Errors: INVALID_ARG (H or W < 1, H*W > 2^40, bad rule, unknown
+ * boundary), UNSUPPORTED (nbhd != 'M'), OOM, CUDA.                          */
 CAT_API int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary,
                cat_handle_t *out);
 
@@ -125,8 +130,10 @@ CAT_API int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int
 CAT_API int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_device,
                   void *stream);
 
-/* Device address and pitch of the current buffer (valid until the next step,
- * set_state or destroy).  For zero-copy inspection; the library owns it.     */
+/* Device address of grid cell (0, 0) of the current buffer and the buffer's
+ * pitch (valid until the next step, set_state or destroy).  For zero-copy
+ * inspection; the library owns it.  With a periodic boundary the address lies
+ * inside the ghost frame's allocation, 16 rows and 16 bytes past its start.   */
 CAT_API int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch);
 
 /* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`

@@ -82,6 +82,7 @@ struct cat_instance {
   cat_rule_t rule{};
   RuleDev rd{};
   int32_t boundary = 0;
+  int32_t ghost = 0;       // periodic: ghost-frame width around the grid (16), else 0
   int32_t kernel = CAT_KERNEL_TCGEN05, dtype = CAT_DTYPE_FP8_E4M3;
   uint8_t *buf[2] = {nullptr, nullptr};
   int cur = 0;
@@ -90,6 +91,8 @@ struct cat_instance {
   DeviceInfo dev;
   int32_t inject = 0;
   uint64_t timeout_ns = 2000000000ull;
+  // grid cell (0, 0) of buffer b (past the ghost frame when there is one)
+  uint8_t *origin(int b) const { return buf[b] + ghost * pitch + ghost; }
 };
 
 namespace {
@@ -137,9 +140,11 @@ int make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, ui
 int build_maps(cat_instance *h) {
   for (int b = 0; b < 2; ++b) {
     int rc;
-    if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, h->W, h->pitch, 128, 160, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
-    if ((rc = make_map(&h->maps[b][1], h->buf[b], h->H, h->W, h->pitch, 32, 160, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
-    if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, h->W, h->pitch, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    // the maps span the buffer including any ghost frame
+    const int64_t H = h->H + 2 * h->ghost, W = h->W + 2 * h->ghost;
+    if ((rc = make_map(&h->maps[b][0], h->buf[b], H, W, h->pitch, 128, 160, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = make_map(&h->maps[b][1], h->buf[b], H, W, h->pitch, 32, 160, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    if ((rc = make_map(&h->maps[b][2], h->buf[b], H, W, h->pitch, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
   }
   return CAT_OK;
 }
@@ -148,8 +153,13 @@ int build_maps(cat_instance *h) {
 int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStream_t s) {
   cudaError_t e;
   if (h->kernel == CAT_KERNEL_TCGEN05) {
+    if (h->ghost) {  // periodic: refresh the input's ghost frame first
+      e = cat::ghost_fill_launch(h->buf[in], h->pitch, h->H, h->W, h->ghost, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ghost-frame launch");
+    }
     cat::TcParams p;
     memset(&p, 0, sizeof(p));
+    p.ox = p.oy = h->ghost;
     p.map_in_a = h->maps[in][0];
     p.map_in_b = h->maps[in][1];
     p.map_out = h->maps[1 - in][2];
@@ -167,6 +177,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
     e = cat::tc_launch(p, h->dtype, h->rule.C > 2, grid, s);
   } else {
+    if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
     cat::SimpleParams p;
     memset(&p, 0, sizeof(p));
     p.in = h->buf[in];
@@ -329,18 +340,19 @@ int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, c
     return fail(CAT_ERR_INVALID_ARG, "grid %lld x %lld is too large", (long long)H, (long long)W);
   int rc = validate_rule(rule);
   if (rc) return rc;
-  if (boundary == CAT_BOUNDARY_PERIODIC) return fail(CAT_ERR_UNSUPPORTED, "periodic boundary is not served yet");
-  if (boundary != CAT_BOUNDARY_ZERO) return fail(CAT_ERR_INVALID_ARG, "unknown boundary %d", boundary);
+  if (boundary != CAT_BOUNDARY_ZERO && boundary != CAT_BOUNDARY_PERIODIC)
+    return fail(CAT_ERR_INVALID_ARG, "unknown boundary %d", boundary);
   cat_instance *h = new (std::nothrow) cat_instance();
   if (!h) return fail(CAT_ERR_OOM, "host allocation failed");
   if ((rc = device_info(&h->dev))) { delete h; return rc; }
   h->H = H;
   h->W = W;
-  h->pitch = round_up(W, 16);
+  h->boundary = boundary;
+  h->ghost = boundary == CAT_BOUNDARY_PERIODIC ? 16 : 0;
+  h->pitch = round_up(W + 2 * h->ghost, 16);
   h->rule = *rule;
   h->rd = reduce_rule(*rule);
-  h->boundary = boundary;
-  const size_t bytes = (size_t)(h->pitch * H);
+  const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
   cudaError_t e = cudaMalloc(&h->buf[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 256);
@@ -375,6 +387,8 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves FP16 and INT8 operands");
   if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
+  if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
+    return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
   h->kernel = kernel;
   h->dtype = dtype;
   return CAT_OK;
@@ -389,19 +403,19 @@ int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src
   (void)src_on_device;  // unified addressing tells host and device memory apart
   if (!h || !src) return fail(CAT_ERR_INVALID_ARG, "NULL handle or source");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
-  return copy2d(h->buf[h->cur], h->pitch, src, pitch, h->W, h->H, (cudaStream_t)stream);
+  return copy2d(h->origin(h->cur), h->pitch, src, pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
 int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_device, void *stream) {
   (void)dst_on_device;
   if (!h || !dst) return fail(CAT_ERR_INVALID_ARG, "NULL handle or destination");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
-  return copy2d(dst, pitch, h->buf[h->cur], h->pitch, h->W, h->H, (cudaStream_t)stream);
+  return copy2d(dst, pitch, h->origin(h->cur), h->pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
 int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch) {
   if (!h || !dptr || !pitch) return fail(CAT_ERR_INVALID_ARG, "NULL argument");
-  *dptr = h->buf[h->cur];
+  *dptr = h->origin(h->cur);
   *pitch = h->pitch;
   return CAT_OK;
 }
@@ -426,9 +440,9 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   }
   if (count == 0 || n_steps == 0) return CAT_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  bool all_tc = true;
+  bool all_tc = true;   // and all with the zero boundary: periodic instances step one by one
   for (int32_t i = 0; i < count; ++i) {
-    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05;
+    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0;
     if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
       return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
     if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)

@@ -30,6 +30,7 @@ struct BatchInst {
   RuleDev rule;
   int32_t H, W, cur, pad;
   int32_t *err;
+  int32_t ox, oy, pad2[2];  // TMA coordinates of grid cell (0, 0) (the ghost-frame width)
 };
 
 // One 128 x 128 output tile of a batched launch.
@@ -48,6 +49,7 @@ struct TcParams {
   CUtensorMap map_out;   // output buffer, box 128 x 128 bytes, 128B swizzle
   CUtensorMap map_ctr;   // input buffer, box 128 x 128 bytes, 128B swizzle (centre tile)
   int32_t H, W, tiles_x, n_tiles;
+  int32_t ox, oy;   // TMA coordinates of grid cell (0, 0): 16 with a periodic ghost frame, else 0
   RuleDev rule;
   int32_t *err;     // device status word (0 = ok)
   int32_t *sums;    // non-null: write box counts here instead of stepping
@@ -86,6 +88,11 @@ int host_validate_rule(const cat_rule_t *r);
 RuleDev host_reduce_rule(const cat_rule_t &r);
 int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, uint32_t box_x,
                   uint32_t box_y, int swizzle128);
+
+// Periodic boundary (cat_halo.cu): fills the G-cell ghost frame around the
+// H x W grid whose cell (0, 0) is at base + G * pitch + G with the cells the
+// frame wraps to.
+cudaError_t ghost_fill_launch(uint8_t *base, int64_t pitch, int64_t H, int64_t W, int G, cudaStream_t s);
 
 // Paper-style fragment kernels (cat_mma.cu).  dt: FP16 or INT8.
 cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s);

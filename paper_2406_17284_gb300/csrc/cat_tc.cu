@@ -294,7 +294,8 @@ __device__ __forceinline__ float half_hi(uint32_t h2) { return __high2float(as_h
 // What one output tile needs: its maps, origin, grid extent and rule.
 struct Tile {
   const CUtensorMap *in_a, *in_b, *out, *ctr;
-  int x0, y0, H, W;
+  int x0, y0, H, W;     // tile origin in grid cells, grid extent
+  int tx0, ty0;         // tile origin in TMA coordinates (x0 + ox, y0 + oy)
   RuleDev R;
   int32_t *err;
 };
@@ -348,6 +349,8 @@ struct TileSeq {
       t.ctr = &I->map_out[in];
       t.x0 = bt.tx * kTile;
       t.y0 = bt.ty * kTile;
+      t.tx0 = t.x0 + I->ox;
+      t.ty0 = t.y0 + I->oy;
       t.H = I->H;
       t.W = I->W;
       t.R = I->rule;
@@ -359,6 +362,8 @@ struct TileSeq {
       t.ctr = &p.map_ctr;
       t.x0 = tx * kTile;
       t.y0 = ty * kTile;
+      t.tx0 = t.x0 + p.ox;
+      t.ty0 = t.y0 + p.oy;
       t.H = p.H;
       t.W = p.W;
       t.R = p.rule;
@@ -450,8 +455,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
-        tma_load_2d(xs, t.in_a, t.x0 - 16, t.y0 - 16, &bars->x_full[s]);
-        tma_load_2d(xs + kWin * 128, t.in_b, t.x0 + 112, t.y0 - 16, &bars->x_full[s]);
+        tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(xs + kWin * 128, t.in_b, t.tx0 + 112, t.ty0 - 16, &bars->x_full[s]);
         issued = j + 1;
       }
       volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const Tile t = lseq.get(p);
         if (j == 0 || BATCH) prefetch_tmap(t.ctr);
         mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.x0, t.y0, &bars->c_full[k]);
+        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.tx0, t.ty0, &bars->c_full[k]);
         lseq.next(p);
         issued = j + 1;
       };
@@ -524,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const Tile t = sseq.get(p);
         if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
         if (BATCH || !p.sums) {
-          tma_store_2d(t.out, t.x0, t.y0, smem + L::kRing + k * L::kRingBytes);
+          tma_store_2d(t.out, t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
           bulk_commit();
           bulk_wait_read<0>();          // the store has read the entry
         }

@@ -51,7 +51,7 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
         (10, 10, cat.make_rule(1, 2, 2, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 0, -1, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 0, 2, 3, 3, 3, nbhd="N"), 0, cat.CAT_ERR_UNSUPPORTED),
-        (10, 10, good, 1, cat.CAT_ERR_UNSUPPORTED),
+        (10, 10, good, -1, cat.CAT_ERR_INVALID_ARG),   # boundaries: 0 zero, 1 periodic
         (10, 10, good, 7, cat.CAT_ERR_INVALID_ARG),
         (1 << 40, 1 << 20, good, 0, cat.CAT_ERR_INVALID_ARG),
     ]
