@@ -233,13 +233,6 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
   tmem_wait_st();
 }
 
-// Next state of one cell from its box count s and state c (see RuleDev).
-__device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev &R) {
-  if (c == 0) return (uint32_t)(s - R.b_lo) <= (uint32_t)R.b_w;
-  if (c == 1) return ((uint32_t)(s - R.s_lo) <= (uint32_t)R.s_w) ? 1u : (R.C > 2 ? 2u : 0u);
-  return (c + 1 == (uint32_t)R.C) ? 0u : c + 1;
-}
-
 // The rule's two ranges as f16 pairs, scaled like the accumulator (S * scale).
 // A lower bound above any count (1089) makes the range empty; an upper bound
 // above it is clamped to 2048.  All values are exact in f16.
@@ -286,6 +279,29 @@ __device__ __forceinline__ uint32_t rule4_binary_h(uint32_t s01, uint32_t s23, u
   uint32_t neg;   // bytes 1, 3 of t01 and 5, 7 of t23 (the sign bytes), sign-replicated
   asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(neg) : "r"(h2_bits(t01)), "r"(h2_bits(t23)));
   return ~neg & 0x01010101u;
+}
+
+// 0x01 in each byte of w that is not zero, else 0x00 (no carry between bytes:
+// (b & 0x7F) + 0x7F <= 0xFE; bit 7 of the sum or of b is set iff b != 0).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t w) {
+  return ((((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) >> 7) & 0x01010101u;
+}
+
+// 4 next states (C > 2) from counts packed as f16 pairs and 4 centre bytes
+// (states 0 .. C-1), four cells per 32-bit word: a dead cell (0) is born into
+// state 1 when its count is in the birth range; an alive cell (1) stays alive
+// in the survival range and otherwise starts dying (state 2); a dying cell
+// (c >= 2) ages to c + 1, and to 0 after state C - 1.  Cb = C in every byte.
+__device__ __forceinline__ uint32_t rule4_multistate_h(uint32_t s01, uint32_t s23, uint32_t cw, const HalfRule &h,
+                                                       uint32_t Cb) {
+  const uint32_t nonzero = nonzero_bytes(cw);                       // c >= 1
+  const uint32_t dying = nonzero_bytes((cw >> 1) & 0x7F7F7F7Fu);    // c >= 2
+  const uint32_t alive = nonzero ^ dying;                           // c == 1
+  const uint32_t dead = nonzero ^ 0x01010101u;                      // c == 0
+  const uint32_t inr = rule4_binary_h(s01, s23, nonzero, h);        // birth range (c = 0) or survival range
+  const uint32_t inc = cw + 0x01010101u;                            // c + 1 <= C <= 255: no carries
+  const uint32_t aged = inc & (nonzero_bytes(inc ^ Cb) * 0xFFu);    // c + 1, or 0 where c + 1 == C
+  return (inr & dead) | ((0x02020202u - inr) & (alive * 0xFFu)) | (aged & (dying * 0xFFu));
 }
 
 __device__ __forceinline__ float half_lo(uint32_t h2) { return __low2float(as_h2(h2)); }
@@ -709,36 +725,30 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
             ov.w = rule4_binary_h(v[c][6], v[c][7], cv.w, hr);
             *cell = ov;
           }
-        } else {
+        } else if (!sums_mode) {
+          const uint32_t Cb = (uint32_t)R.C * 0x01010101u;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
+            const uint4 cv = *cell;
+            uint4 ov;
+            ov.x = rule4_multistate_h(v[c][0], v[c][1], cv.x, hr, Cb);
+            ov.y = rule4_multistate_h(v[c][2], v[c][3], cv.y, hr, Cb);
+            ov.z = rule4_multistate_h(v[c][4], v[c][5], cv.z, hr, Cb);
+            ov.w = rule4_multistate_h(v[c][6], v[c][7], cv.w, hr, Cb);
+            *cell = ov;
+          }
+        } else {   // box counts
+          const int gy = t.y0 + y;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int cc = kq + 4 * c;
-            uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
-            const uint4 cv = *cell;
-            const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w};
-            int cnt[16];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              cnt[2 * i] = __float2int_rn(half_lo(v[c][i]) * (1.0f / kScale));
-              cnt[2 * i + 1] = __float2int_rn(half_hi(v[c][i]) * (1.0f / kScale));
-            }
-            if (sums_mode) {
-              const int gy = t.y0 + y;
-#pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int gx = t.x0 + 16 * cc + i;
-                if (gy < t.H && gx < t.W) p.sums[(int64_t)gy * p.sums_ld + gx] = cnt[i];
-              }
-            } else {
-              uint32_t ow[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                uint32_t word = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) word |= next_state(cnt[4 * i + b], (cw[i] >> (8 * b)) & 0xFFu, R) << (8 * b);
-                ow[i] = word;
-              }
-              *cell = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+            for (int i = 0; i < 16; ++i) {
+              const uint32_t h2 = v[c][i >> 1];
+              const float s = (i & 1) ? half_hi(h2) : half_lo(h2);
+              const int gx = t.x0 + 16 * cc + i;
+              if (gy < t.H && gx < t.W) p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(s * (1.0f / kScale));
             }
           }
         }
