@@ -87,7 +87,9 @@ struct cat_instance {
   uint8_t *buf[2] = {nullptr, nullptr};
   int cur = 0;
   int32_t *d_err = nullptr;
-  CUtensorMap maps[2][3];  // per buffer: in_a, in_b, out
+  // per buffer: window boxes 128 x 160 and 32 x 160, the 128 x 128 tile box,
+  // and the window boxes of the short-window kernel, 128 x 144 and 32 x 144
+  CUtensorMap maps[2][5];
   DeviceInfo dev;
   int32_t inject = 0;
   uint64_t timeout_ns = 2000000000ull;
@@ -145,8 +147,16 @@ int build_maps(cat_instance *h) {
     if ((rc = make_map(&h->maps[b][0], h->buf[b], H, W, h->pitch, 128, 160, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
     if ((rc = make_map(&h->maps[b][1], h->buf[b], H, W, h->pitch, 32, 160, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
     if ((rc = make_map(&h->maps[b][2], h->buf[b], H, W, h->pitch, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = make_map(&h->maps[b][3], h->buf[b], H, W, h->pitch, 128, 144, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = make_map(&h->maps[b][4], h->buf[b], H, W, h->pitch, 32, 144, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
   }
   return CAT_OK;
+}
+
+// The short-window kernel serves FP8 operands on two-state rules with r <= 7
+// (pass 2 then runs on e4m3, and 128 + 2r window rows fit in 144).
+bool short_window(const cat_instance *h) {
+  return h->kernel == CAT_KERNEL_TCGEN05 && h->dtype == CAT_DTYPE_FP8_E4M3 && h->rule.C == 2 && h->rule.r <= 7;
 }
 
 // One step of instance h from buffer `in` into buffer 1 - in (or box sums into `sums`).
@@ -160,8 +170,9 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     cat::TcParams p;
     memset(&p, 0, sizeof(p));
     p.ox = p.oy = h->ghost;
-    p.map_in_a = h->maps[in][0];
-    p.map_in_b = h->maps[in][1];
+    const bool sw = short_window(h);
+    p.map_in_a = h->maps[in][sw ? 3 : 0];
+    p.map_in_b = h->maps[in][sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
     p.map_ctr = h->maps[in][2];
     p.H = (int32_t)h->H;
@@ -175,7 +186,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.timeout_ns = h->timeout_ns;
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
-    e = cat::tc_launch(p, h->dtype, h->rule.C > 2, grid, s);
+    e = cat::tc_launch(p, h->dtype, h->rule.C > 2, sw, grid, s);
   } else {
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
     cat::SimpleParams p;
@@ -203,6 +214,7 @@ struct BatchPlan {
   int64_t steps_done = 0;     // steps advanced through this plan since then
   int32_t dtype = 0;
   bool encode = false;
+  bool sw = false;            // every instance qualifies for the short-window kernel
   cat::BatchInst *d_inst = nullptr;
   cat::BatchTile *d_tiles = nullptr;
   int n_tiles = 0, grid = 0;
@@ -244,8 +256,8 @@ int upload_instances(BatchPlan *pl) {
   for (size_t i = 0; i < pl->hs.size(); ++i) {
     const cat_instance *h = pl->hs[i];
     for (int b = 0; b < 2; ++b) {
-      inst[i].map_in_a[b] = h->maps[b][0];
-      inst[i].map_in_b[b] = h->maps[b][1];
+      inst[i].map_in_a[b] = h->maps[b][pl->sw ? 3 : 0];
+      inst[i].map_in_b[b] = h->maps[b][pl->sw ? 4 : 1];
       inst[i].map_out[b] = h->maps[b][2];
     }
     inst[i].rule = h->rd;
@@ -272,6 +284,8 @@ int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
   pl->dtype = hs[0]->dtype;
   pl->encode = false;
   for (int32_t i = 0; i < count; ++i) pl->encode |= hs[i]->rule.C > 2;
+  pl->sw = true;
+  for (int32_t i = 0; i < count; ++i) pl->sw &= short_window(hs[i]);
   // work-list: instances ordered by radius, tiles row-major within an instance
   std::vector<int> order(count);
   for (int32_t i = 0; i < count; ++i) order[i] = i;
@@ -306,7 +320,7 @@ int launch_batch_steps(BatchPlan *pl, int64_t n_steps, int64_t start, cudaStream
   p.btiles = pl->d_tiles;
   for (int64_t t = 0; t < n_steps; ++t) {
     p.parity = (int32_t)((start + t) & 1);
-    cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pl->encode, pl->grid, s);
+    cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pl->encode, pl->sw, pl->grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   }
   return CAT_OK;

@@ -77,9 +77,11 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 // tcgen05 kernel launchers (cat_tc.cu).  dt: CAT_DTYPE_FP16 or CAT_DTYPE_FP8_E4M3.
 // encode: FP8 only -- stage the operand through an encoded copy of the window
 // (needed when C > 2; otherwise the raw 0/1 bytes are used as e4m3 operands).
-cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
-cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s);
-size_t tc_smem_bytes(int dt, bool encode);
+// sw: short-window variant (FP8 operands, C = 2, r <= 7): map_in_a / map_in_b
+// must then be the maps with 144-row window boxes.
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
+cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
+size_t tc_smem_bytes(int dt, bool encode, bool sw);
 
 // Host helpers defined in cat_api.cu (error message of the calling thread,
 // rule checks, TMA descriptor encoding of a uint8 grid).

@@ -144,7 +144,7 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
   p.binst = slot->ptr->inst;
   p.btiles = slot->ptr->tiles;
   const int grid = (int)(n_tiles < slot->sms ? n_tiles : slot->sms);
-  e = cat::tc_launch_batch(p, dtype, encode, grid, s);
+  e = cat::tc_launch_batch(p, dtype, encode, false, grid, s);
   if (e != cudaSuccess) return err(CAT_ERR_CUDA, "batched launch failed (%lld)", (long long)e);
   // the host image is copied from pageable memory: the copies have consumed it
   // before cudaMemcpyAsync returned, so the next call may overwrite it

@@ -63,10 +63,28 @@ constexpr int kEpiWarps = 16;                      // four per TMEM lane quarter
 constexpr int kCvtThreads = 32 * kCvtWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 128 + kCvtThreads + kEpiThreads;
-constexpr int kRegions = 2;                        // accumulator regions (D1, then D2 of a tile)
-constexpr int kRegionCols = 160;
-constexpr uint32_t kTmemBand16 = 320;              // f16 band as the A operand: 80 columns
-constexpr uint32_t kTmemBand8 = 416;               // e4m3 band (FP8 kernel): 40 columns
+constexpr int kMaxRegions = 3;
+
+// Window geometry and tensor memory, by kernel variant.  The standard window
+// is 160 x 160 starting 16 cells above and left of the tile; two 160-column
+// accumulator regions (D1, then D2 of a tile) leave room for the f16 band (80
+// columns, pass 2 when 2r+1 > 15 and the FP16 kernel) and the e4m3 band (40).
+// Short window (SW, FP8 with r <= 7, where pass 2 runs on e4m3): the window
+// holds 144 rows starting 8 above the tile (TMA y-coordinates need no
+// alignment), so pass 1 has N = 144 and three 144-column regions fit beside
+// two e4m3 bands -- pass 1's (window columns offset by 16) and pass 2's
+// (window rows offset by 8): 3 * 144 + 40 + 40 = 512.  Three tiles are then in
+// flight instead of two.
+template <bool SW>
+struct Geo {
+  static constexpr int kRows = SW ? 144 : 160;        // window rows = pass-1 N
+  static constexpr int kYOff = SW ? 8 : 16;           // window rows above the tile
+  static constexpr int kRegions = SW ? 3 : 2;
+  static constexpr int kRegionCols = SW ? 144 : 160;
+  static constexpr uint32_t kBand16 = 320;            // f16 band (standard only)
+  static constexpr uint32_t kBand8 = SW ? 432 : 416;  // e4m3 band, offset 16 (pass 1; also pass 2 if standard)
+  static constexpr uint32_t kBand8P2 = SW ? 472 : 416;  // e4m3 band for pass 2 (offset kYOff)
+};
 constexpr uint32_t kTmemCols = 512;
 
 // Byte offset of the element at byte position kb (= k * E) of row `row` in a
@@ -125,30 +143,33 @@ __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDe
 // also serves as the output staging (the epilogue overwrites each centre state
 // with the next state in place), so the 160 x 160 window stage is free as
 // soon as pass 1 (or the encoding) has read it.
-template <int DT, bool ENC>
+template <int DT, bool ENC, bool SW = false>
 struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
-  static constexpr int NS = (DT == 0 || ENC) ? 2 : 3;         // TMA window stages
-  static constexpr int NR = DT == 0 ? 2 : 3;                  // centre / output ring
-  static constexpr int NH = 2;                                // pass-2 operand buffers
+  static constexpr int NS = SW ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
+  static constexpr int NR = SW ? 4 : (DT == 0 ? 2 : 3);       // centre / output ring
+  static constexpr int NH = SW ? 3 : 2;                       // pass-2 operand buffers
   static constexpr uint32_t kXs = 0;                          // u8 windows (TMA)
-  static constexpr uint32_t kXsBytes = kWin * kWin;
-  static constexpr uint32_t kXe = kXs + NS * kXsBytes;        // encoded window
+  static constexpr uint32_t kXsBytes = kWin * Geo<SW>::kRows;  // bytes one window load delivers
+  static constexpr uint32_t kXsStride = (kXsBytes + 1023) / 1024 * 1024;  // 128B-swizzle atoms stay aligned
+  static constexpr uint32_t kXe = kXs + NS * kXsStride;       // encoded window
   static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E1 : 0;
-  static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand
-  static constexpr uint32_t kHBytes = kTile * kWin * 2;
+  static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand (K padded to 160)
+  static constexpr uint32_t kHBytes = kTile * kWin * (SW ? 1 : 2);
   static constexpr uint32_t kRing = kH + NH * kHBytes;        // centre tiles / output staging
   static constexpr uint32_t kRingBytes = kTile * kTile;
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
   static_assert(kDyn <= 232448, "shared memory budget");
+  static_assert(kXe % 1024 == 0 && kH % 1024 == 0 && kRing % 1024 == 0 && kHBytes % 1024 == 0,
+                "swizzled operands start on 1024-byte boundaries");
 };
 
 struct Bars {
-  uint64_t x_full[3], x_empty[3];
-  uint64_t c_full[3], out_full[3];
-  uint64_t d1_full[kRegions], d2_full[kRegions], tmem_empty[kRegions];
-  uint64_t h_full[2], enc_full, band_ready;
+  uint64_t x_full[4], x_empty[4];
+  uint64_t c_full[4], out_full[4];
+  uint64_t d1_full[kMaxRegions], d2_full[kMaxRegions], tmem_empty[kMaxRegions];
+  uint64_t h_full[3], enc_full, band_ready;
   uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
@@ -195,40 +216,48 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
   }
 }
 
-// Band B[m][k] = one iff k - m in [16 - r, 16 + r] as the A operand in tensor
-// memory: row m in lane m, K packed along the columns (two f16 values, or
-// four e4m3 values, per column, the lowest k in the low bits).  The f16 band
-// takes 80 columns, the e4m3 band (FP8 kernel) 40.  Convert warp (q, kq)
-// writes lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
-template <int DT>
+// Band B[m][k] = one iff k - m in [off - r, off + r] as an A operand in tensor
+// memory: row m in lane m, K packed along the columns (two f16 values, or four
+// e4m3 values, per column, the lowest k in the low bits); 80 columns (f16) or
+// 40 (e4m3).  Standard kernels hold the f16 band (FP16 kernel and pass 2 when
+// 2r+1 > 15) and, in the FP8 kernel, the e4m3 band, both with offset 16;
+// short-window kernels hold two e4m3 bands, offset 16 (pass 1) and offset 8
+// (pass 2).  Convert warp (q, kq) writes lanes 32q .. 32q+31 and every other
+// 8-column chunk from chunk kq.
+template <int DT, bool SW>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
-  constexpr int kChunks16 = 10, kChunks = DT == 1 ? 15 : 10;
+  using G = Geo<SW>;
+  // chunks [0, n0) belong to the first band, [n0, n) to the second
+  constexpr int n0 = SW ? 5 : 10, n = SW ? 10 : (DT == 1 ? 15 : 10);
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
-  for (int c = kq; c < kChunks; c += 2) {          // warp-uniform
-    const bool f16 = c < kChunks16;
-    const int cc = f16 ? c : c - kChunks16;
+  for (int c = kq; c < n; c += 2) {                 // warp-uniform
+    const bool first = c < n0;
+    const bool f16 = !SW && first;
+    const int cc = first ? c : c - n0;
+    const int off = (SW && !first) ? G::kYOff : 16;
+    const uint32_t col = SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : G::kBand8);
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int col = 8 * cc + i;
+      const int k0 = (f16 ? 2 : 4) * (8 * cc + i);
       uint32_t w = 0;
       if (f16) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          const int d = 2 * col + b - m;
-          if (d >= 16 - r && d <= 16 + r) w |= 0x3C00u << (16 * b);
+          const int d = k0 + b - m;
+          if (d >= off - r && d <= off + r) w |= 0x3C00u << (16 * b);
         }
       } else {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          const int d = 4 * col + b - m;
-          if (d >= 16 - r && d <= 16 + r) w |= 0x38u << (8 * b);
+          const int d = k0 + b - m;
+          if (d >= off - r && d <= off + r) w |= 0x38u << (8 * b);
         }
       }
       v[i] = w;
     }
-    tmem_st8(tmem + la + (f16 ? kTmemBand16 : kTmemBand8) + 8 * cc, v);
+    tmem_st8(tmem + la + col + 8 * cc, v);
   }
   tmem_wait_st();
 }
@@ -406,9 +435,12 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 // exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
-template <int DT, bool ENC, bool BATCH>
+template <int DT, bool ENC, bool BATCH, bool SW>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
-  using L = Layout<DT, ENC>;
+  using L = Layout<DT, ENC, SW>;
+  using G = Geo<SW>;
+  constexpr int kRegions = G::kRegions;
+  constexpr int kRegionCols = G::kRegionCols;
   constexpr int E1 = L::E1;
   constexpr int NS = L::NS;
   constexpr int NR = L::NR;
@@ -426,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&bars->x_full[i], 1);
       mbar_init(&bars->x_empty[i], ENC ? kCvtWarps : 1);  // encoders, or pass 1's commit
       mbar_init(&bars->c_full[i], 1);
@@ -437,8 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       mbar_init(&bars->d2_full[i], 1);
       mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
-    mbar_init(&bars->h_full[0], kCvtWarps);
-    mbar_init(&bars->h_full[1], kCvtWarps);
+    for (int i = 0; i < 3; ++i) mbar_init(&bars->h_full[i], kCvtWarps);
     mbar_init(&bars->enc_full, kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
     mbar_init(&bars->mma_done[0], 1);
@@ -450,6 +481,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   if (warp == 1) {
     tmem_alloc(&bars->tmem_base, kTmemCols);
     tmem_relinquish();
+  }
+  if constexpr (SW) {  // pass-2 operand columns 144..159 (K padding) stay zero
+    for (int i = threadIdx.x; i < (int)(L::NH * L::kHBytes / 16); i += kThreads)
+      reinterpret_cast<uint4 *>(smem + L::kH)[i] = make_uint4(0, 0, 0, 0);
   }
   fence_proxy_async_smem();
   tc_fence_before();
@@ -469,10 +504,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const Tile t = seq.get(p);
         if (j == 0 || BATCH) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
         if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
-        uint8_t *xs = smem + L::kXs + s * L::kXsBytes;
+        uint8_t *xs = smem + L::kXs + s * L::kXsStride;
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
-        tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - 16, &bars->x_full[s]);
-        tma_load_2d(xs + kWin * 128, t.in_b, t.tx0 + 112, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - G::kYOff, &bars->x_full[s]);
+        tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 + 112, t.ty0 - G::kYOff, &bars->x_full[s]);
         issued = j + 1;
       }
       volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
@@ -488,8 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     if (lane == 0) {
       // f16 accumulators: every partial sum is a multiple of the operand scale
       // up to 1089 * scale, which f16 represents exactly
-      const uint32_t idesc1 = idesc_f16acc(128, kWin);
-      const uint32_t band1 = tmem + (DT == 1 ? kTmemBand8 : kTmemBand16);
+      const uint32_t idesc1 = idesc_f16acc(128, G::kRows);
+      const uint32_t band1 = tmem + (DT == 1 ? G::kBand8 : G::kBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -510,9 +545,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         else ok = mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
         if (!ok) { set_abort(bars, err0, 6); break; }
         tc_fence_after();
-        const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsBytes) >> 4);   // window stage
+        const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsStride) >> 4);   // window stage
         const OpDesc win{win0.d128 + soff, win0.d32 + soff};
-        band_mma<DT == 0 ? 0 : 1, kWin, E1>(tmem + reg * kRegionCols, band1, win, idesc1);
+        band_mma<DT == 0 ? 0 : 1, G::kRows, E1>(tmem + reg * kRegionCols, band1, win, idesc1);
         mma_commit(&bars->d1_full[reg]);
         if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
       }
@@ -561,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     // D2 of tile j over its D1 region once the convert warps have written H.
     if (lane == 0) {
       const uint32_t idesc2 = idesc_f16acc(128, kTile);
-      const uint32_t band16 = tmem + kTmemBand16, band8 = tmem + kTmemBand8;
+      const uint32_t band16 = tmem + G::kBand16, band8 = tmem + G::kBand8P2;
       const OpDesc hop0 = op_descs(s_base + L::kH);
       for (int j = 0; j < n_my; ++j) {
         if (!mbar_wait(&bars->h_full[j % NH], (j / NH) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, err0, 9); break; }
@@ -599,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
     // the bands for the first tile
-    store_bands<DT>(tmem, r0, q, kq, lane);
+    store_bands<DT, SW>(tmem, r0, q, kq, lane);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -622,7 +657,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         // every pass 2 so far (tile j-1 last) has finished reading the bands
         if (NH > 1 && j >= 1 && !(ok = warp_wait(&bars->d2_full[(j - 1) % kRegions], ((j - 1) / kRegions) & 1, bars, p.timeout_ns))) break;
         tc_fence_after();
-        store_bands<DT>(tmem, rj, q, kq, lane);
+        store_bands<DT, SW>(tmem, rj, q, kq, lane);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -635,12 +670,17 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         // are already the pass-2 operand (or become e4m3 pairs with one cvt)
         const uint32_t treg = tmem + lane_addr + reg * kRegionCols + 80 * kq;
         uint8_t *hop = smem + L::kH + (j % NH) * L::kHBytes;
+        // V has kRows columns: 10 chunks of 16, or 9 in a short window (the
+        // second warp of a quarter then takes 4)
+        const bool last = !SW || kq == 0;           // this warp converts chunk 4 of its five
         uint32_t v[5][8];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) tmem_ld16_pack16(treg + 16 * c, v[c]);
+        for (int c = 0; c < 4; ++c) tmem_ld16_pack16(treg + 16 * c, v[c]);
+        if (last) tmem_ld16_pack16(treg + 64, v[4]);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
+          if (c == 4 && !last) break;
           if (p2f16) {
             *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]);
             *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(v[c][4], v[c][5], v[c][6], v[c][7]);
@@ -666,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const int s1 = (j + 1) % NS;
         const bool ms1 = tile_rule<BATCH>(p, first, j + 1).C > 2;
         if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
-        encode_window<E1>(smem + L::kXs + s1 * L::kXsBytes, smem + L::kXe, ms1, wtid, kCvtThreads);
+        encode_window<E1>(smem + L::kXs + s1 * L::kXsStride, smem + L::kXe, ms1, wtid, kCvtThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[s1]); }
@@ -771,34 +811,39 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 }  // namespace tc
 
 // dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
-size_t tc_smem_bytes(int dt, bool encode) {
+size_t tc_smem_bytes(int dt, bool encode, bool sw) {
   if (dt == 1) return tc::Layout<0, true>::kDyn;
+  if (sw) return tc::Layout<1, false, true>::kDyn;
   return encode ? tc::Layout<1, true>::kDyn : tc::Layout<1, false>::kDyn;
 }
 
-template <int DT, bool ENC, bool BATCH>
+template <int DT, bool ENC, bool BATCH, bool SW = false>
 static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
   static bool configured = false;
-  const size_t smem = tc::Layout<DT, ENC>::kDyn;
+  const size_t smem = tc::Layout<DT, ENC, SW>::kDyn;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH>,
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH, SW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_tc_kernel<DT, ENC, BATCH><<<grid, tc::kThreads, smem, s>>>(p);
+  tc::ltl_tc_kernel<DT, ENC, BATCH, SW><<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
+// sw: the short-window variant (FP8, two-state rules, r <= 7); the caller
+// passes the tensor maps whose window boxes are 144 rows high.
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s) {
   if (dt == 1) return launch_one<0, true, false>(p, grid, s);
   if (encode) return launch_one<1, true, false>(p, grid, s);
+  if (sw) return launch_one<1, false, false, true>(p, grid, s);
   return launch_one<1, false, false>(p, grid, s);
 }
 
-cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, int grid, cudaStream_t s) {
+cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s) {
   if (dt == 1) return launch_one<0, true, true>(p, grid, s);
   if (encode) return launch_one<1, true, true>(p, grid, s);
+  if (sw) return launch_one<1, false, true, true>(p, grid, s);
   return launch_one<1, false, true>(p, grid, s);
 }
 

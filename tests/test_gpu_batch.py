@@ -24,13 +24,13 @@ def orule(d):
     return oracle.Rule(d["r"], d["C"], d["M"], d["s1"], d["s2"], d["b1"], d["b2"])
 
 
-def make_batch(seed, count, lo, hi, multistate=False):
+def make_batch(seed, count, lo, hi, multistate=False, r_max=16):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         H = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
         W = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
-        r = int(rng.integers(1, 17))
+        r = int(rng.integers(1, r_max + 1))
         M = int(rng.integers(0, 2))
         if multistate and i % 2 == 0:
             C = int(rng.choice([3, 5, 16]))
@@ -41,7 +41,7 @@ def make_batch(seed, count, lo, hi, multistate=False):
             grid = inputs.bernoulli(H, W, float(rng.uniform(0.2, 0.6)), seed * 1000 + i)
         out.append((grid, rule))
     out.append((inputs.bernoulli(1, 1, 1.0, 1), inputs.scaled_rule(3, 0)))   # degenerate shapes
-    out.append((inputs.bernoulli(1, 300, 0.5, 2), inputs.scaled_rule(16, 1)))
+    out.append((inputs.bernoulli(1, 300, 0.5, 2), inputs.scaled_rule(min(16, r_max), 1)))
     out.append((inputs.bernoulli(129, 1, 0.5, 3), inputs.scaled_rule(2, 1)))
     return out
 
@@ -71,6 +71,12 @@ def check_batch(cat, batch, steps_list, kernel="tcgen05", dtype="fp8", individua
 @pytest.mark.parametrize("dtype", ["fp8", "fp16"])
 def test_batch_mixed_sizes_radii_rules(cat, dtype):
     check_batch(cat, make_batch(1, 40, 8, 700), [5], dtype=dtype)
+
+
+def test_batch_small_radii_short_window(cat):
+    # every grid has r <= 7 and C = 2: the FP8 batch runs the short-window kernel
+    # (three tiles in flight, both e4m3 bands rebuilt whenever the radius changes)
+    check_batch(cat, make_batch(6, 40, 8, 700, r_max=7), [3, 2])
 
 
 def test_batch_graph_replay_odd_steps(cat):
