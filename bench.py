@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--radii", default="1-16", help="radii to run, e.g. 1-16 or 16 or 1,8,16")
     ap.add_argument("--batch-count", type=int, default=4096, help="grids in the batched workload (0: skip it)")
     ap.add_argument("--multistate-size", type=int, default=49152, help="side of the multi-state grid (0: skip it)")
+    ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
     return ap.parse_args()
 
 
@@ -282,6 +283,22 @@ def measure_multistate(args, torch, cat, inputs, stream):
     return out
 
 
+def measure_periodic(args, torch, cat, inputs, stream, radii=(1, 8, 16)):
+    """The same 16384^2 Bernoulli(0.5) grid and scaled rules with the periodic
+    boundary (each step = ghost-frame refresh + tcgen05 step), FP8 operands."""
+    n = args.size
+    init = inputs.bernoulli(n, n, 0.5, SEED)
+    out = {"workload": f"{n}x{n} periodic, scaled rule C2 M1, fp8"}
+    for r in radii:
+        g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype="fp8", boundary=cat.BOUNDARY_PERIODIC)
+        g.set_state(init)
+        g.step(1, stream)
+        t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
+        out[f"r{r}_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
+        g.close()
+    return out
+
+
 def run_cat(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -399,6 +416,9 @@ def run_cat(args, rank, world, local):
     multistate = None
     if args.multistate_size > 0 and rank == 0:
         multistate = measure_multistate(args, torch, cat, inputs, stream)
+    periodic = None
+    if not args.no_periodic and rank == 0:
+        periodic = measure_periodic(args, torch, cat, inputs, stream)
 
     cpu = None
     if rank == 0:
@@ -428,6 +448,7 @@ def run_cat(args, rank, world, local):
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
             "batched": batched,
             "multistate": multistate,
+            "periodic": periodic,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,
