@@ -52,6 +52,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_rate(ms_total_local, cells_per_step_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` replicas: the slowest rank's time over
+    `steps` steps, and every rank's cells.  Returns (ms per step, cells/s)."""
+    import torch
+    ms = float(ms_total_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / steps
+    return ms_per_step, cells_per_step_per_rank * world / (ms_per_step / 1000.0)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -354,18 +367,12 @@ def run_cat(args, rank, world, local):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms_total = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
     for g in grids.values():
         rc = g.status()
         if rc != cat.CAT_OK:
             raise RuntimeError(f"device status {rc}")
-    ms_per_step = ms_total / args.steps
     cells_per_step = n * n * len(RADII)
-    value = cells_per_step * world / (ms_per_step / 1000.0)
+    ms_per_step, value = job_rate(t0.elapsed_time(t1), cells_per_step, args.steps, world, dist, dev)
     launch_ms = {}
     for r, a, b in per_launch:
         launch_ms.setdefault(r, []).append(a.elapsed_time(b))
