@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096, help="grids in the batched workload (0: skip it)")
     ap.add_argument("--multistate-size", type=int, default=49152, help="side of the multi-state grid (0: skip it)")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
+    ap.add_argument("--no-bits", action="store_true", help="skip the one-bit-storage measurement")
     return ap.parse_args()
 
 
@@ -312,6 +313,38 @@ def measure_periodic(args, torch, cat, inputs, stream, radii=(1, 8, 16)):
     return out
 
 
+def measure_bits(args, torch, cat, inputs, stream, d_init, hbm, reps=3):
+    """One-bit storage: the headline's 16384^2 grid and 16 scaled rules stored 8 cells
+    per byte (FP8 operands), stepped round-robin over the radii like the headline, so
+    16 x 64 MiB pass between two steps of one grid (more than L2).  The algorithmic
+    traffic is 1/8 byte read + 1/8 byte written per cell update."""
+    n = args.size
+    grids = {r: cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype="fp8", storage=cat.STORE_BIT1)
+             for r in RADII}
+    for g in grids.values():
+        g.set_state(d_init)
+    for r in RADII:
+        grids[r].step(1, stream)
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in RADII]
+           for _ in range(reps)]
+    for row in evs:
+        for (a, b), r in zip(row, RADII):
+            a.record(stream)
+            grids[r].step(1, stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    per_r = {r: statistics.median(row[i][0].elapsed_time(row[i][1]) for row in evs) for i, r in enumerate(RADII)}
+    for g in grids.values():
+        assert g.status() == cat.CAT_OK
+        g.close()
+    ms = sum(per_r.values())
+    achieved = 0.25 * n * n * len(RADII) / (ms / 1000.0) / 1e9
+    return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, one bit per cell, fp8",
+            "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
+            "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
+            "bytes_per_cell": 0.25, "achieved_gbs": achieved, "hbm_frac": achieved / hbm}
+
+
 def run_cat(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -426,6 +459,9 @@ def run_cat(args, rank, world, local):
     periodic = None
     if not args.no_periodic and rank == 0:
         periodic = measure_periodic(args, torch, cat, inputs, stream)
+    bits = None
+    if not args.no_bits and rank == 0:
+        bits = measure_bits(args, torch, cat, inputs, stream, d_init, hbm)
 
     cpu = None
     if rank == 0:
@@ -456,6 +492,7 @@ def run_cat(args, rank, world, local):
             "batched": batched,
             "multistate": multistate,
             "periodic": periodic,
+            "bits": bits,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,

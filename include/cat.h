@@ -77,6 +77,16 @@ enum {
   CAT_DTYPE_FP4_E2M1 = 4
 };
 
+/* How the instance stores its grid in device memory.
+ *   U8    one byte per cell (the cell's state), W bytes per row.
+ *   BIT1  one bit per cell, for two-state rules (C = 2): cell x of a row is
+ *         bit x % 8 of byte x / 8 (lowest x in the lowest bit), so a row takes
+ *         ceil(W / 8) bytes and the bits past W in the last byte stay 0.  An
+ *         eighth of the HBM traffic of U8.  Stepped by the TCGEN05 kernel on
+ *         FP8 operands with the zero boundary; cat_batch_step advances BIT1
+ *         instances one launch per instance and step.  The state is still
+ *         passed in and out one byte per cell (cat_set_state/cat_get_state
+ *         convert on the device); cat_state_ptr exposes the packed rows.      */
 enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1 };
 
 /* Which kernel advances the grid.
@@ -111,11 +121,25 @@ typedef struct cat_instance *cat_handle_t;
 CAT_API int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary,
                cat_handle_t *out);
 
-/* Chooses the kernel and operand dtype used by later steps (defaults:
- * CAT_KERNEL_AUTO -> TCGEN05, CAT_DTYPE_AUTO -> FP8_E4M3 for TCGEN05, FP16 for
- * MMA_SYNC).  storage must be CAT_STORE_U8; steps_per_launch must be 1.
- * Errors: INVALID_ARG for unknown values, UNSUPPORTED for combinations this
- * build does not serve (e.g. TCGEN05 + INT8: sm_103a has no tcgen05 kind::i8). */
+/* cat_create with the storage chosen up front, so that a one-bit grid never
+ * holds the byte-per-cell buffers (a CAT_STORE_BIT1 grid of 2^40 cells takes
+ * 2 x 128 GiB).  storage is CAT_STORE_U8 (same as cat_create) or
+ * CAT_STORE_BIT1 (C = 2 and the zero boundary; options default to TCGEN05 +
+ * FP8_E4M3).  Errors: as cat_create, INVALID_ARG for an unknown storage,
+ * UNSUPPORTED for BIT1 with C != 2 or a periodic boundary.                  */
+CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary,
+                  int32_t storage, cat_handle_t *out);
+
+/* Chooses the kernel, operand dtype and storage used by later steps
+ * (defaults: CAT_KERNEL_AUTO -> TCGEN05, CAT_DTYPE_AUTO -> FP8_E4M3 for
+ * TCGEN05, FP16 for MMA_SYNC; instances start with CAT_STORE_U8).  A change
+ * of storage reallocates both buffers and converts the current grid (the
+ * device is synchronised; earlier cat_state_ptr addresses become invalid).
+ * CAT_STORE_BIT1 needs C = 2, the zero boundary, TCGEN05 and FP8_E4M3.
+ * steps_per_launch must be 1.  Errors: INVALID_ARG for unknown values,
+ * UNSUPPORTED for combinations this build does not serve (e.g. TCGEN05 +
+ * INT8: sm_103a has no tcgen05 kind::i8), OOM, CUDA.  After INVALID_ARG,
+ * UNSUPPORTED or OOM the instance keeps its previous options and state.     */
 CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage,
                     int32_t steps_per_launch);
 
@@ -133,7 +157,9 @@ CAT_API int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t d
 /* Device address of grid cell (0, 0) of the current buffer and the buffer's
  * pitch (valid until the next step, set_state or destroy).  For zero-copy
  * inspection; the library owns it.  With a periodic boundary the address lies
- * inside the ghost frame's allocation, 16 rows and 16 bytes past its start.   */
+ * inside the ghost frame's allocation, 16 rows and 16 bytes past its start.
+ * With CAT_STORE_BIT1 it holds the packed rows (pitch = ceil(W / 8) rounded
+ * up to 16 bytes).                                                          */
 CAT_API int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch);
 
 /* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`

@@ -34,7 +34,7 @@ DTYPES = {"auto": DTYPE_AUTO, "fp16": DTYPE_FP16, "fp8": DTYPE_FP8_E4M3, "int8":
 KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MMA_SYNC,
            "stencil": KERNEL_STENCIL}
 
-EXPORTED = ["cat_create", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
+EXPORTED = ["cat_create", "cat_create_ex", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
             "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
             "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static"]
 
@@ -82,6 +82,7 @@ def load(path: str | None = None):
         h, i32, i64, p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         sig = {
             "cat_create": [i64, i64, ctypes.POINTER(cat_rule_t), i32, ctypes.POINTER(ctypes.c_void_p)],
+            "cat_create_ex": [i64, i64, ctypes.POINTER(cat_rule_t), i32, i32, ctypes.POINTER(ctypes.c_void_p)],
             "cat_set_options": [h, i32, i32, i32, i32],
             "cat_set_state": [h, p, i64, i32, p],
             "cat_get_state": [h, p, i64, i32, p],
@@ -129,6 +130,12 @@ def make_rule(r: int, C: int, M: int, s1: int, s2: int, b1: int, b2: int, nbhd: 
 def cat_create(H: int, W: int, rule: cat_rule_t, boundary: int = BOUNDARY_ZERO) -> int:
     out = ctypes.c_void_p()
     _check(load().cat_create(H, W, ctypes.byref(rule), boundary, ctypes.byref(out)))
+    return out.value
+
+
+def cat_create_ex(H: int, W: int, rule: cat_rule_t, boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8) -> int:
+    out = ctypes.c_void_p()
+    _check(load().cat_create_ex(H, W, ctypes.byref(rule), boundary, storage, ctypes.byref(out)))
     return out.value
 
 
@@ -192,13 +199,15 @@ class Grid:
     """One LTL instance: owns a cat handle; state in/out as numpy or torch tensors."""
 
     def __init__(self, H: int, W: int, rule: dict, kernel: str = "tcgen05", dtype: str = "fp8",
-                 boundary: int = BOUNDARY_ZERO):
+                 boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8):
         self.H, self.W = int(H), int(W)
         self.rule = dict(rule)
-        self.handle = cat_create(self.H, self.W, make_rule(**{k: rule[k] for k in
-                                                              ("r", "C", "M", "s1", "s2", "b1", "b2")}), boundary)
+        self.storage = int(storage)
+        self.handle = cat_create_ex(self.H, self.W, make_rule(**{k: rule[k] for k in
+                                                                 ("r", "C", "M", "s1", "s2", "b1", "b2")}),
+                                    boundary, self.storage)
         try:
-            cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype])
+            cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage)
         except Exception:
             cat_destroy(self.handle)
             raise
@@ -235,14 +244,16 @@ class Grid:
         return out
 
     def state_tensor(self):
-        """Zero-copy torch view of the current device buffer (H x pitch, uint8)."""
+        """Zero-copy torch view of the current device buffer (H x pitch, uint8):
+        H x W cells, or H x ceil(W / 8) packed bytes with one-bit storage."""
         import torch
         ptr, pitch = cat_state_ptr(self.handle)
 
         class _Arr:
             __cuda_array_interface__ = {"shape": (self.H, pitch), "typestr": "|u1",
                                         "data": (ptr, False), "version": 3}
-        return torch.as_tensor(_Arr(), device="cuda")[:, : self.W]
+        cols = (self.W + 7) // 8 if self.storage == STORE_BIT1 else self.W
+        return torch.as_tensor(_Arr(), device="cuda")[:, :cols]
 
     def step(self, n_steps: int = 1, stream=None):
         cat_step(self.handle, n_steps, stream)

@@ -83,6 +83,7 @@ struct cat_instance {
   RuleDev rd{};
   int32_t boundary = 0;
   int32_t ghost = 0;       // periodic: ghost-frame width around the grid (16), else 0
+  int32_t storage = CAT_STORE_U8;  // BIT1: one bit per cell, (W + 7) / 8 bytes per row
   int32_t kernel = CAT_KERNEL_TCGEN05, dtype = CAT_DTYPE_FP8_E4M3;
   uint8_t *buf[2] = {nullptr, nullptr};
   int cur = 0;
@@ -140,6 +141,16 @@ int make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, ui
 }
 
 int build_maps(cat_instance *h) {
+  if (h->storage == CAT_STORE_BIT1) {  // packed rows: 48 x 160-byte windows, 16 x 128-byte tiles
+    for (int b = 0; b < 2; ++b) {
+      int rc;
+      const int64_t wb = (h->W + 7) / 8;
+      if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, wb, h->pitch, 48, 160, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+      if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, wb, h->pitch, 16, 128, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][0];
+    }
+    return CAT_OK;
+  }
   for (int b = 0; b < 2; ++b) {
     int rc;
     // the maps span the buffer including any ghost frame
@@ -170,7 +181,8 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     cat::TcParams p;
     memset(&p, 0, sizeof(p));
     p.ox = p.oy = h->ghost;
-    const bool sw = short_window(h);
+    const bool bits = h->storage == CAT_STORE_BIT1;
+    const bool sw = !bits && short_window(h);
     p.map_in_a = h->maps[in][sw ? 3 : 0];
     p.map_in_b = h->maps[in][sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
@@ -186,7 +198,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.timeout_ns = h->timeout_ns;
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
-    e = cat::tc_launch(p, h->dtype, h->rule.C > 2, sw, grid, s);
+    e = cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
   } else {
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
     cat::SimpleParams p;
@@ -340,6 +352,80 @@ int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitc
 }
 }  // namespace cat
 
+namespace {
+
+// Rows per chunk when a uint8 grid passes through a temporary device buffer
+// on its way to or from one-bit storage (64 MiB at most).
+int64_t chunk_rows(int64_t W) { return std::max<int64_t>(1, std::min<int64_t>(4096, (64ll << 20) / W)); }
+
+// Reallocates the state of h in `storage`, converting the current grid.
+int change_storage(cat_instance *h, int32_t storage) {
+  const int64_t pitch = storage == CAT_STORE_BIT1 ? round_up((h->W + 7) / 8, 16) : round_up(h->W, 16);
+  const size_t bytes = (size_t)(pitch * h->H);
+  uint8_t *nb[2] = {nullptr, nullptr};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMalloc(&nb[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&nb[1], bytes);
+  if (e == cudaSuccess) e = cudaMemset(nb[0], 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(nb[1], 0, bytes);
+  if (e == cudaSuccess)
+    e = storage == CAT_STORE_BIT1 ? cat::pack_bits_launch(h->origin(h->cur), h->pitch, nb[0], pitch, h->H, h->W, 0)
+                                  : cat::unpack_bits_launch(h->origin(h->cur), h->pitch, nb[0], pitch, h->H, h->W, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(nb[0]);
+    cudaFree(nb[1]);
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(CAT_ERR_OOM, "device allocation of %zu bytes failed", bytes)
+                                          : cuda_fail(e, "storage change");
+  }
+  drop_plans_with(h);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  h->buf[0] = nb[0];
+  h->buf[1] = nb[1];
+  h->cur = 0;
+  h->pitch = pitch;
+  h->storage = storage;
+  return build_maps(h);
+}
+
+// uint8 rows <-> one-bit storage through a temporary device buffer.
+int bits_set_state(cat_instance *h, const uint8_t *src, int64_t pitch, cudaStream_t s) {
+  const int64_t R = chunk_rows(h->W);
+  uint8_t *tmp = nullptr;
+  CAT_CUDA(cudaMalloc(&tmp, (size_t)(R * h->W)));
+  cudaError_t e = cudaSuccess;
+  for (int64_t y = 0; y < h->H && e == cudaSuccess; y += R) {
+    const int64_t n = std::min(R, h->H - y);
+    e = cudaMemcpy2DAsync(tmp, (size_t)h->W, src + y * pitch, (size_t)pitch, (size_t)h->W, (size_t)n, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cat::pack_bits_launch(tmp, h->W, h->buf[h->cur] + y * h->pitch, h->pitch, n, h->W, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "cat_set_state (one-bit storage)");
+  return CAT_OK;
+}
+
+int bits_get_state(cat_instance *h, uint8_t *dst, int64_t pitch, cudaStream_t s) {
+  const int64_t R = chunk_rows(h->W);
+  uint8_t *tmp = nullptr;
+  CAT_CUDA(cudaMalloc(&tmp, (size_t)(R * h->W)));
+  cudaError_t e = cudaSuccess;
+  for (int64_t y = 0; y < h->H && e == cudaSuccess; y += R) {
+    const int64_t n = std::min(R, h->H - y);
+    e = cat::unpack_bits_launch(h->buf[h->cur] + y * h->pitch, h->pitch, tmp, h->W, n, h->W, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dst + y * pitch, (size_t)pitch, tmp, (size_t)h->W, (size_t)h->W, (size_t)n, cudaMemcpyDefault, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "cat_get_state (one-bit storage)");
+  return CAT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *cat_last_error(void) { return g_err; }
@@ -347,6 +433,11 @@ const char *cat_last_error(void) { return g_err; }
 const char *cat_version(void) { return "cat-gb300 0.1 (sm_103a)"; }
 
 int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, cat_handle_t *out) {
+  return cat_create_ex(H, W, rule, boundary, CAT_STORE_U8, out);
+}
+
+int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, int32_t storage,
+                  cat_handle_t *out) {
   if (!out) return fail(CAT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (H < 1 || W < 1) return fail(CAT_ERR_INVALID_ARG, "grid %lld x %lld is empty", (long long)H, (long long)W);
@@ -356,6 +447,10 @@ int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, c
   if (rc) return rc;
   if (boundary != CAT_BOUNDARY_ZERO && boundary != CAT_BOUNDARY_PERIODIC)
     return fail(CAT_ERR_INVALID_ARG, "unknown boundary %d", boundary);
+  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
+  if (storage == CAT_STORE_BIT1 && rule->C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
+  if (storage == CAT_STORE_BIT1 && boundary != CAT_BOUNDARY_ZERO)
+    return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
   cat_instance *h = new (std::nothrow) cat_instance();
   if (!h) return fail(CAT_ERR_OOM, "host allocation failed");
   if ((rc = device_info(&h->dev))) { delete h; return rc; }
@@ -363,7 +458,8 @@ int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary, c
   h->W = W;
   h->boundary = boundary;
   h->ghost = boundary == CAT_BOUNDARY_PERIODIC ? 16 : 0;
-  h->pitch = round_up(W + 2 * h->ghost, 16);
+  h->storage = storage;
+  h->pitch = storage == CAT_STORE_BIT1 ? round_up((W + 7) / 8, 16) : round_up(W + 2 * h->ghost, 16);
   h->rule = *rule;
   h->rd = reduce_rule(*rule);
   const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
@@ -391,7 +487,6 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (dtype < CAT_DTYPE_AUTO || dtype > CAT_DTYPE_FP4_E2M1) return fail(CAT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
   if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
-  if (storage != CAT_STORE_U8) return fail(CAT_ERR_UNSUPPORTED, "only uint8 storage is served yet");
   if (steps_per_launch != 1) return fail(CAT_ERR_UNSUPPORTED, "only one step per launch is served yet");
   if (kernel == CAT_KERNEL_AUTO) kernel = CAT_KERNEL_TCGEN05;
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
@@ -403,6 +498,16 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
   if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
     return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
+  if (storage == CAT_STORE_BIT1) {
+    if (h->rule.C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
+    if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
+    if (kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3)
+      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 operands");
+  }
+  if (storage != h->storage) {
+    int rc = change_storage(h, storage);
+    if (rc) return rc;
+  }
   h->kernel = kernel;
   h->dtype = dtype;
   return CAT_OK;
@@ -417,6 +522,7 @@ int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src
   (void)src_on_device;  // unified addressing tells host and device memory apart
   if (!h || !src) return fail(CAT_ERR_INVALID_ARG, "NULL handle or source");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
+  if (h->storage == CAT_STORE_BIT1) return bits_set_state(h, src, pitch, (cudaStream_t)stream);
   return copy2d(h->origin(h->cur), h->pitch, src, pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
@@ -424,6 +530,7 @@ int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_de
   (void)dst_on_device;
   if (!h || !dst) return fail(CAT_ERR_INVALID_ARG, "NULL handle or destination");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
+  if (h->storage == CAT_STORE_BIT1) return bits_get_state(h, dst, pitch, (cudaStream_t)stream);
   return copy2d(dst, pitch, h->origin(h->cur), h->pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
@@ -454,9 +561,9 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   }
   if (count == 0 || n_steps == 0) return CAT_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  bool all_tc = true;   // and all with the zero boundary: periodic instances step one by one
+  bool all_tc = true;   // zero boundary, uint8 storage: other instances step one by one
   for (int32_t i = 0; i < count; ++i) {
-    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0;
+    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8;
     if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
       return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
     if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)

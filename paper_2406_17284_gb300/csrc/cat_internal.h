@@ -79,7 +79,9 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 // (needed when C > 2; otherwise the raw 0/1 bytes are used as e4m3 operands).
 // sw: short-window variant (FP8 operands, C = 2, r <= 7): map_in_a / map_in_b
 // must then be the maps with 144-row window boxes.
-cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
+// bits: one bit per cell (FP8, C = 2, single instance): map_in_a is the 48 x
+// 160-byte window map and map_out / map_ctr the 16 x 128-byte tile maps.
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits, int grid, cudaStream_t s);
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
 size_t tc_smem_bytes(int dt, bool encode, bool sw);
 
@@ -90,6 +92,14 @@ int host_validate_rule(const cat_rule_t *r);
 RuleDev host_reduce_rule(const cat_rule_t &r);
 int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, uint32_t box_x,
                   uint32_t box_y, int swizzle128);
+
+// One bit per cell (cat_bits.cu): rows of W cells <-> rows of (W + 7) / 8
+// bytes, cell x in bit x % 8 of byte x / 8; pack writes bit 1 for state 1 and
+// zeros past W in each row's last byte.
+cudaError_t pack_bits_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
+                             int64_t W, cudaStream_t s);
+cudaError_t unpack_bits_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
+                               int64_t W, cudaStream_t s);
 
 // Periodic boundary (cat_halo.cu): fills the G-cell ghost frame around the
 // H x W grid whose cell (0, 0) is at base + G * pitch + G with the cells the

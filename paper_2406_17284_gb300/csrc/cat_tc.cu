@@ -143,25 +143,31 @@ __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDe
 // also serves as the output staging (the epilogue overwrites each centre state
 // with the next state in place), so the 160 x 160 window stage is free as
 // soon as pass 1 (or the encoding) has read it.
-template <int DT, bool ENC, bool SW = false>
+// BITS: the grid is stored one bit per cell (8 cells per byte, lowest x in the
+// lowest bit); a window stage is then one 48-byte x 160-row box (cells x0 - 128
+// .. x0 + 255, of which the window uses x0 - 16 .. x0 + 143) that the convert
+// warps unpack into the e4m3 operand, and a ring entry is 16 bytes x 128 rows.
+template <int DT, bool ENC, bool SW = false, bool BITS = false>
 struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
-  static constexpr int NS = SW ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
-  static constexpr int NR = SW ? 4 : (DT == 0 ? 2 : 3);       // centre / output ring
+  static constexpr int NS = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
+  static constexpr int NR = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
+  static constexpr int NE = (DT == 1 && ENC) ? 2 : 1;         // encoded windows (FP8: encode ahead)
   static constexpr int NH = SW ? 3 : 2;                       // pass-2 operand buffers
-  static constexpr uint32_t kXs = 0;                          // u8 windows (TMA)
-  static constexpr uint32_t kXsBytes = kWin * Geo<SW>::kRows;  // bytes one window load delivers
+  static constexpr uint32_t kXs = 0;                          // raw windows (TMA)
+  static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : kWin * Geo<SW>::kRows;  // bytes one window load delivers
   static constexpr uint32_t kXsStride = (kXsBytes + 1023) / 1024 * 1024;  // 128B-swizzle atoms stay aligned
   static constexpr uint32_t kXe = kXs + NS * kXsStride;       // encoded window
-  static constexpr uint32_t kXeBytes = ENC ? kWin * kWin * E1 : 0;
+  static constexpr uint32_t kXeStride = kWin * kWin * E1;     // one encoded window (25 or 50 KiB)
+  static constexpr uint32_t kXeBytes = ENC ? NE * kXeStride : 0;
   static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand (K padded to 160)
   static constexpr uint32_t kHBytes = kTile * kWin * (SW ? 1 : 2);
   static constexpr uint32_t kRing = kH + NH * kHBytes;        // centre tiles / output staging
-  static constexpr uint32_t kRingBytes = kTile * kTile;
+  static constexpr uint32_t kRingBytes = BITS ? 16 * kTile : kTile * kTile;
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
   static_assert(kDyn <= 232448, "shared memory budget");
-  static_assert(kXe % 1024 == 0 && kH % 1024 == 0 && kRing % 1024 == 0 && kHBytes % 1024 == 0,
+  static_assert(kXe % 1024 == 0 && kXeStride % 1024 == 0 && kH % 1024 == 0 && kRing % 1024 == 0 && kHBytes % 1024 == 0,
                 "swizzled operands start on 1024-byte boundaries");
 };
 
@@ -169,7 +175,7 @@ struct Bars {
   uint64_t x_full[4], x_empty[4];
   uint64_t c_full[4], out_full[4];
   uint64_t d1_full[kMaxRegions], d2_full[kMaxRegions], tmem_empty[kMaxRegions];
-  uint64_t h_full[3], enc_full, band_ready;
+  uint64_t h_full[3], enc_full[2], band_ready;
   uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
@@ -213,6 +219,25 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
       *reinterpret_cast<uint4 *>(xe + op_off(kWin, 2, row, 32 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<uint4 *>(xe + op_off(kWin, 2, row, 32 * c + 16)) = make_uint4(h[4], h[5], h[6], h[7]);
     }
+  }
+}
+
+// Four cells' bits (bits 0..3 of n) -> four bytes 0/1 (no carries: the four
+// shifted copies of n land on disjoint bit ranges).
+__device__ __forceinline__ uint32_t bits4_to_bytes(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
+
+// Four bytes 0/1 -> four bits (byte b to bit b): the multiplier moves byte b's
+// low bit to bit 24 + b and every other product term below bit 24 or above 31.
+__device__ __forceinline__ uint32_t bytes_to_bits4(uint32_t w) { return (w * 0x01020408u) >> 24 & 0xFu; }
+
+// Unpacks a bit-packed window stage (160 rows of 48 bytes, window cell x' at
+// bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell.
+__device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
+  for (int q = tid; q < kWin * 10; q += nthr) {
+    const int c = q / kWin, row = q - c * kWin;
+    const uint32_t b = *reinterpret_cast<const uint16_t *>(xs + row * 48 + 14 + 2 * c);
+    *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
+        make_uint4(bits4_to_bytes(b), bits4_to_bytes(b >> 4), bits4_to_bytes(b >> 8), bits4_to_bytes(b >> 12));
   }
 }
 
@@ -435,9 +460,10 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 // exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
-template <int DT, bool ENC, bool BATCH, bool SW>
+template <int DT, bool ENC, bool BATCH, bool SW, bool BITS>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
-  using L = Layout<DT, ENC, SW>;
+  static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
+  using L = Layout<DT, ENC, SW, BITS>;
   using G = Geo<SW>;
   constexpr int kRegions = G::kRegions;
   constexpr int kRegionCols = G::kRegionCols;
@@ -470,7 +496,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
     for (int i = 0; i < 3; ++i) mbar_init(&bars->h_full[i], kCvtWarps);
-    mbar_init(&bars->enc_full, kCvtWarps);
+    mbar_init(&bars->enc_full[0], kCvtWarps);
+    mbar_init(&bars->enc_full[1], kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
     mbar_init(&bars->mma_done[0], 1);
     mbar_init(&bars->mma_done[1], 1);
@@ -506,8 +533,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *xs = smem + L::kXs + s * L::kXsStride;
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
-        tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - G::kYOff, &bars->x_full[s]);
-        tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 + 112, t.ty0 - G::kYOff, &bars->x_full[s]);
+        if constexpr (BITS) {   // bytes x0/8 - 16 .. x0/8 + 31: 16-byte aligned
+          tma_load_2d(xs, t.in_a, t.tx0 / 8 - 16, t.ty0 - 16, &bars->x_full[s]);
+        } else {
+          tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - G::kYOff, &bars->x_full[s]);
+          tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 + 112, t.ty0 - G::kYOff, &bars->x_full[s]);
+        }
         issued = j + 1;
       }
       volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
@@ -541,11 +572,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
           band_r = r;
         }
         if (!(ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 5); break; }
-        if (ENC) ok = mbar_wait(&bars->enc_full, j & 1, &bars->abort, p.timeout_ns);
+        if (ENC) ok = mbar_wait(&bars->enc_full[j % L::NE], (j / L::NE) & 1, &bars->abort, p.timeout_ns);
         else ok = mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
         if (!ok) { set_abort(bars, err0, 6); break; }
         tc_fence_after();
-        const uint64_t soff = ENC ? 0 : (uint64_t)((s * L::kXsStride) >> 4);   // window stage
+        const uint64_t soff = ENC ? (uint64_t)(((j % L::NE) * L::kXeStride) >> 4)   // encoded window
+                                  : (uint64_t)((s * L::kXsStride) >> 4);             // window stage
         const OpDesc win{win0.d128 + soff, win0.d32 + soff};
         band_mma<DT == 0 ? 0 : 1, G::kRows, E1>(tmem + reg * kRegionCols, band1, win, idesc1);
         mma_commit(&bars->d1_full[reg]);
@@ -570,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const Tile t = lseq.get(p);
         if (j == 0 || BATCH) prefetch_tmap(t.ctr);
         mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, t.tx0, t.ty0, &bars->c_full[k]);
+        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
         lseq.next(p);
         issued = j + 1;
       };
@@ -580,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
         const Tile t = sseq.get(p);
         if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
         if (BATCH || !p.sums) {
-          tma_store_2d(t.out, t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
+          tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
           bulk_commit();
           bulk_wait_read<0>();          // the store has read the entry
         }
@@ -638,15 +670,21 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
-    if (ENC && n_my > 0) {
-      ok = warp_wait(&bars->x_full[0], 0, bars, p.timeout_ns);
-      if (ok) {
-        encode_window<E1>(smem + L::kXs, smem + L::kXe, tile_rule<BATCH>(p, first, 0).C > 2, wtid, kCvtThreads);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[0]); }
-      }
-    }
+    // window j goes into encoded buffer j % NE once pass 1 of tile j - NE has
+    // read that buffer: the first NE windows now, the others in the loop
+    auto encode = [&](int j) -> bool {
+      const int s = j % L::NS, e = j % L::NE;
+      if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
+      uint8_t *xe = smem + L::kXe + e * L::kXeStride;
+      if constexpr (BITS) unpack_window(smem + L::kXs + s * L::kXsStride, xe, wtid, kCvtThreads);
+      else encode_window<E1>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, wtid, kCvtThreads);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) { mbar_arrive(&bars->enc_full[e]); mbar_arrive(&bars->x_empty[s]); }
+      return true;
+    };
+    if (ENC)
+      for (int j = 0; ok && j < n_my && j < L::NE; ++j) ok = encode(j);
     for (int j = 0; ok && j < n_my; ++j) {
       const int reg = j % kRegions;
       const int rj = tile_rule<BATCH>(p, first, j).r;
@@ -701,16 +739,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->h_full[j % NH]);
-      // encode the next window (pass 1 of tile j, its reader, has completed)
-      if (ENC && j + 1 < n_my) {
-        const int s1 = (j + 1) % NS;
-        const bool ms1 = tile_rule<BATCH>(p, first, j + 1).C > 2;
-        if (!(ok = warp_wait(&bars->x_full[s1], ((j + 1) / NS) & 1, bars, p.timeout_ns))) break;
-        encode_window<E1>(smem + L::kXs + s1 * L::kXsStride, smem + L::kXe, ms1, wtid, kCvtThreads);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) { mbar_arrive(&bars->enc_full); mbar_arrive(&bars->x_empty[s1]); }
-      }
+      // encode window j + NE into the buffer pass 1 of tile j has finished reading
+      if (ENC && j + L::NE < n_my && !(ok = encode(j + L::NE))) break;
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
@@ -753,7 +783,23 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
       {
         const bool sums_mode = !BATCH && p.sums != nullptr;
-        if (!sums_mode && R.C == 2) {
+        if (BITS && !sums_mode) {
+          // 16 cells of a chunk are 16 bits of the row (lowest x lowest);
+          // cells at x >= W, inside the row's last byte, stay dead
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int cc = kq + 4 * c;
+            uint16_t *cellp = reinterpret_cast<uint16_t *>(ring + y * 16 + 2 * cc);
+            const uint32_t b = *cellp;
+            uint32_t nb = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              nb |= bytes_to_bits4(rule4_binary_h(v[c][2 * i], v[c][2 * i + 1], bits4_to_bytes(b >> (4 * i)), hr)) << (4 * i);
+            const int lim = t.W - (t.x0 + 16 * cc);
+            if (lim < 16) nb &= lim > 0 ? (1u << lim) - 1u : 0u;
+            *cellp = (uint16_t)nb;
+          }
+        } else if (!sums_mode && R.C == 2) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
@@ -817,23 +863,27 @@ size_t tc_smem_bytes(int dt, bool encode, bool sw) {
   return encode ? tc::Layout<1, true>::kDyn : tc::Layout<1, false>::kDyn;
 }
 
-template <int DT, bool ENC, bool BATCH, bool SW = false>
+template <int DT, bool ENC, bool BATCH, bool SW = false, bool BITS = false>
 static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
   static bool configured = false;
-  const size_t smem = tc::Layout<DT, ENC, SW>::kDyn;
+  const size_t smem = tc::Layout<DT, ENC, SW, BITS>::kDyn;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH, SW>,
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH, SW, BITS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_tc_kernel<DT, ENC, BATCH, SW><<<grid, tc::kThreads, smem, s>>>(p);
+  tc::ltl_tc_kernel<DT, ENC, BATCH, SW, BITS><<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 // sw: the short-window variant (FP8, two-state rules, r <= 7); the caller
-// passes the tensor maps whose window boxes are 144 rows high.
-cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s) {
+// passes the tensor maps whose window boxes are 144 rows high.  bits: the
+// grid is stored one bit per cell (FP8, two-state rules, single instance);
+// the caller passes the 48 x 160 window and 16 x 128 tile maps of the packed
+// buffers.
+cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits, int grid, cudaStream_t s) {
+  if (bits) return launch_one<1, true, false, false, true>(p, grid, s);
   if (dt == 1) return launch_one<0, true, false>(p, grid, s);
   if (encode) return launch_one<1, true, false>(p, grid, s);
   if (sw) return launch_one<1, false, false, true>(p, grid, s);
