@@ -152,7 +152,7 @@ struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
   static constexpr int NS = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
   static constexpr int NR = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
-  static constexpr int NE = (DT == 1 && ENC) ? 2 : 1;         // encoded windows (FP8: encode ahead)
+  static constexpr int NE = BITS ? 3 : ((DT == 1 && ENC) ? 2 : 1);  // encoded windows (FP8: encode ahead)
   static constexpr int NH = SW ? 3 : 2;                       // pass-2 operand buffers
   static constexpr uint32_t kXs = 0;                          // raw windows (TMA)
   static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : kWin * Geo<SW>::kRows;  // bytes one window load delivers
@@ -175,7 +175,7 @@ struct Bars {
   uint64_t x_full[4], x_empty[4];
   uint64_t c_full[4], out_full[4];
   uint64_t d1_full[kMaxRegions], d2_full[kMaxRegions], tmem_empty[kMaxRegions];
-  uint64_t h_full[3], enc_full[2], band_ready;
+  uint64_t h_full[3], enc_full[3], band_ready;
   uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
@@ -232,12 +232,24 @@ __device__ __forceinline__ uint32_t bytes_to_bits4(uint32_t w) { return (w * 0x0
 
 // Unpacks a bit-packed window stage (160 rows of 48 bytes, window cell x' at
 // bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell.
+// One item is half a row (80 cells, 16-cell chunks 5h .. 5h+4): three aligned
+// 32-bit loads (bytes 12 + 12h ..), shifted by 16 bits for h = 0 so that the
+// chunks are the five consecutive 16-bit fields.
 __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
-  for (int q = tid; q < kWin * 10; q += nthr) {
-    const int c = q / kWin, row = q - c * kWin;
-    const uint32_t b = *reinterpret_cast<const uint16_t *>(xs + row * 48 + 14 + 2 * c);
-    *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
-        make_uint4(bits4_to_bytes(b), bits4_to_bytes(b >> 4), bits4_to_bytes(b >> 8), bits4_to_bytes(b >> 12));
+  for (int q = tid; q < 2 * kWin; q += nthr) {
+    const int h = q >= kWin ? 1 : 0, row = q - h * kWin;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(xs + row * 48 + 12 + 12 * h);
+    uint32_t a = src[0], b = src[1], c = src[2];
+    if (!h) {
+      a = __funnelshift_r(a, b, 16);
+      b = __funnelshift_r(b, c, 16);
+      c >>= 16;
+    }
+    const uint32_t f[5] = {a, a >> 16, b, b >> 16, c};
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
+          make_uint4(bits4_to_bytes(f[i]), bits4_to_bytes(f[i] >> 4), bits4_to_bytes(f[i] >> 8), bits4_to_bytes(f[i] >> 12));
   }
 }
 
@@ -496,8 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
     for (int i = 0; i < 3; ++i) mbar_init(&bars->h_full[i], kCvtWarps);
-    mbar_init(&bars->enc_full[0], kCvtWarps);
-    mbar_init(&bars->enc_full[1], kCvtWarps);
+    for (int i = 0; i < L::NE; ++i) mbar_init(&bars->enc_full[i], kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
     mbar_init(&bars->mma_done[0], 1);
     mbar_init(&bars->mma_done[1], 1);
@@ -519,6 +530,21 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   const uint32_t s_base = smem_u32(smem);
+
+  // The convert warps encode window j into buffer j % NE once pass 1 of tile
+  // j - NE has read that buffer: the first NE windows before the tile loop,
+  // window j + NE right after converting D1 of tile j.
+  auto encode = [&](int j, int tid, int nthr) -> bool {
+    const int s = j % L::NS, e = j % L::NE;
+    if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
+    uint8_t *xe = smem + L::kXe + e * L::kXeStride;
+    if constexpr (BITS) unpack_window(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
+    else encode_window<L::E1>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, tid, nthr);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) { mbar_arrive(&bars->enc_full[e]); mbar_arrive(&bars->x_empty[s]); }
+    return true;
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------ window producer
@@ -670,21 +696,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
-    // window j goes into encoded buffer j % NE once pass 1 of tile j - NE has
-    // read that buffer: the first NE windows now, the others in the loop
-    auto encode = [&](int j) -> bool {
-      const int s = j % L::NS, e = j % L::NE;
-      if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
-      uint8_t *xe = smem + L::kXe + e * L::kXeStride;
-      if constexpr (BITS) unpack_window(smem + L::kXs + s * L::kXsStride, xe, wtid, kCvtThreads);
-      else encode_window<E1>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, wtid, kCvtThreads);
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) { mbar_arrive(&bars->enc_full[e]); mbar_arrive(&bars->x_empty[s]); }
-      return true;
-    };
     if (ENC)
-      for (int j = 0; ok && j < n_my && j < L::NE; ++j) ok = encode(j);
+      for (int j = 0; ok && j < n_my && j < L::NE; ++j) ok = encode(j, wtid, kCvtThreads);
     for (int j = 0; ok && j < n_my; ++j) {
       const int reg = j % kRegions;
       const int rj = tile_rule<BATCH>(p, first, j).r;
@@ -740,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->h_full[j % NH]);
       // encode window j + NE into the buffer pass 1 of tile j has finished reading
-      if (ENC && j + L::NE < n_my && !(ok = encode(j + L::NE))) break;
+      if (ENC && j + L::NE < n_my && !(ok = encode(j + L::NE, wtid, kCvtThreads))) break;
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
