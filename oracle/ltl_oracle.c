@@ -15,8 +15,17 @@
  *     Only state 1 ("alive") is counted.  The centre cell is counted ONCE
  *     (reading of the "added twice" remark of Sec. IV: the Moore product with
  *     a unit-diagonal band contains the centre once).
+ *  1b. Simplified von Neumann count (Sec. IV, Eq. 3: the second product takes
+ *     Lambda instead of H and adds H, R = Pi*Lambda + Lambda*Pi):
+ *        L(y,x) = sum_{d=-r..r} [ s(y+d, x) == 1 ] + sum_{d=-r..r} [ s(y, x+d) == 1 ]
+ *     the vertical and the horizontal segment through the cell; the centre
+ *     lies on both and is counted TWICE, as the paper states for this form.
  *  2. Middle-cell flag M of the LTL notation R C M S B N (Sec. V-A):
- *        k = L - (M == 0 ? [s(y,x) == 1] : 0)
+ *        Moore:              k = L - (M == 0 ? [s(y,x) == 1] : 0)
+ *        simplified v. N.:   k = L - (M == 0 ? 2 : 1) * [s(y,x) == 1]
+ *     so that k counts the live neighbours, plus the cell itself when M = 1,
+ *     in both neighbourhoods (the paper's "compute R - 2 Lambda" when the
+ *     centre is excluded).
  *  3. Transition (Sec. V-A notation; multi-state decay read as the
  *     Generations-style LTL rule, since the paper only runs C = 2):
  *        s == 0      -> 1 if b1 <= k <= b2 else 0
@@ -25,7 +34,8 @@
  *     All cells update synchronously from the previous grid (ping-pong
  *     buffers of Sec. IV-C).
  *
- * No blocking, fusion or reordering: one plain (2r+1)^2 loop per cell.  The
+ * No blocking, fusion or reordering: one plain (2r+1)^2 loop per cell (two
+ * (2r+1) loops for the simplified von Neumann count).  The
  * only liberty taken is clipping the dy/dx loop ranges to the grid for the
  * zero boundary (the skipped terms are the ghost zeros).  Rows are spread
  * over OpenMP threads; every cell is independent.
@@ -46,6 +56,7 @@
 
 typedef struct {
   int32_t r, C, M, s1, s2, b1, b2;
+  int32_t nbhd; /* 0: Moore box (Eqs. 1-2); 1: simplified von Neumann cross (Eq. 3) */
 } oracle_rule;
 
 enum { ORACLE_ZERO = 0, ORACLE_PERIODIC = 1 };
@@ -87,11 +98,38 @@ static int32_t box_count(const uint8_t *g, int64_t H, int64_t W, int64_t ld,
   return n;
 }
 
+/* L(y,x) of Eq. 3: state-1 cells on the vertical and on the horizontal segment
+ * of half-length r through (y,x); the centre is on both and counts twice. */
+static int32_t cross_count(const uint8_t *g, int64_t H, int64_t W, int64_t ld,
+                           int64_t y, int64_t x, int r, int boundary) {
+  int32_t n = 0;
+  for (int d = -r; d <= r; ++d) {
+    const int64_t yy = y + d, xx = x + d;
+    if (boundary == ORACLE_PERIODIC) {
+      n += g[wrap(yy, H) * ld + x] == 1;
+#if ORACLE_MUTATION == 6 /* the horizontal segment misses the centre */
+      if (d != 0)
+#endif
+      n += g[y * ld + wrap(xx, W)] == 1;
+    } else {
+      if (yy >= 0 && yy < H) n += g[yy * ld + x] == 1;
+#if ORACLE_MUTATION == 6
+      if (d != 0)
+#endif
+      if (xx >= 0 && xx < W) n += g[y * ld + xx] == 1;
+    }
+  }
+  return n;
+}
+
 static uint8_t transition(uint8_t s, int32_t L, const oracle_rule *R) {
 #if ORACLE_MUTATION == 3 /* centre handling inverted (subtract when M == 1) */
   int32_t k = L - ((R->M == 1) ? (s == 1) : 0);
-#else
+#elif ORACLE_MUTATION == 7 /* the cross takes the Moore centre handling */
   int32_t k = L - ((R->M == 0) ? (s == 1) : 0);
+#else
+  int32_t k = R->nbhd == 1 ? L - (R->M == 0 ? 2 : 1) * (s == 1)
+                           : L - ((R->M == 0) ? (s == 1) : 0);
 #endif
   if (s == 0) {
 #if ORACLE_MUTATION == 4 /* off-by-one in the birth range */
@@ -119,6 +157,7 @@ static int check_args(int64_t H, int64_t W, int64_t ld, int r, int boundary) {
 
 static int check_rule(const oracle_rule *R) {
   if (!R || R->r < 0 || R->C < 2 || R->C > 256 || (R->M != 0 && R->M != 1)) return -1;
+  if (R->nbhd != 0 && R->nbhd != 1) return -1;
   return 0;
 }
 
@@ -132,6 +171,16 @@ int oracle_box_sums(const uint8_t *g, int64_t H, int64_t W, int64_t ld, int r,
   return 0;
 }
 
+/* S[y*lds + x] = the simplified von Neumann count L(y,x) of Eq. 3. */
+int oracle_cross_sums(const uint8_t *g, int64_t H, int64_t W, int64_t ld, int r,
+                      int boundary, int32_t *S, int64_t lds) {
+  if (!g || !S || check_args(H, W, ld, r, boundary) || lds < W) return -1;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t y = 0; y < H; ++y)
+    for (int64_t x = 0; x < W; ++x) S[y * lds + x] = cross_count(g, H, W, ld, y, x, r, boundary);
+  return 0;
+}
+
 /* out = one synchronous LTL step of in. */
 int oracle_step(const uint8_t *in, uint8_t *out, int64_t H, int64_t W, int64_t ld,
                 const oracle_rule *R, int boundary) {
@@ -142,7 +191,8 @@ int oracle_step(const uint8_t *in, uint8_t *out, int64_t H, int64_t W, int64_t l
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t y = 0; y < H; ++y)
     for (int64_t x = 0; x < W; ++x) {
-      int32_t L = box_count(in, H, W, ld, y, x, R->r, boundary);
+      int32_t L = R->nbhd == 1 ? cross_count(in, H, W, ld, y, x, R->r, boundary)
+                               : box_count(in, H, W, ld, y, x, R->r, boundary);
       out[y * ld + x] = transition(in[y * ld + x], L, R);
     }
   return 0;

@@ -6,7 +6,8 @@ never imports it; the two sides share only the seeded input generators.
 
 The arithmetic lives in ``ltl_oracle.c`` (a plain per-cell (2r+1)^2 loop, see its
 header for the passages of the CAT paper it follows: Sec. IV Eqs. 1-2 for the
-box count, Sec. V-A for the R C M S B N rule).  This file compiles it with gcc
+box count, Eq. 3 for the simplified von Neumann count, Sec. V-A for the
+R C M S B N rule).  This file compiles it with gcc
 and marshals numpy arrays into it.
 """
 from __future__ import annotations
@@ -29,7 +30,8 @@ PERIODIC = 1
 
 @dataclass(frozen=True)
 class Rule:
-    """LTL rule R_r C_c M_m S_{s1..s2} B_{b1..b2} N_M (Sec. V-A notation)."""
+    """LTL rule R_r C_c M_m S_{s1..s2} B_{b1..b2} N_n (Sec. V-A notation); nbhd "M" is
+    the Moore box, "N" the simplified von Neumann cross of Eq. 3."""
 
     r: int
     C: int
@@ -38,10 +40,17 @@ class Rule:
     s2: int
     b1: int
     b2: int
+    nbhd: str = "M"
 
 
 class _CRule(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("r", "C", "M", "s1", "s2", "b1", "b2")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("r", "C", "M", "s1", "s2", "b1", "b2", "nbhd")]
+
+
+def _crule(rule: Rule) -> _CRule:
+    if rule.nbhd not in ("M", "N"):
+        raise ValueError(f"unknown neighbourhood {rule.nbhd!r}")
+    return _CRule(rule.r, rule.C, rule.M, rule.s1, rule.s2, rule.b1, rule.b2, 1 if rule.nbhd == "N" else 0)
 
 
 def compile_oracle(out_dir: str | None = None, mutation: int = 0) -> str:
@@ -68,9 +77,11 @@ _lock = threading.Lock()
 def _bind(lib):
     i64, i32, p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
     lib.oracle_box_sums.argtypes = [p, i64, i64, i64, i32, i32, p, i64]
+    lib.oracle_cross_sums.argtypes = [p, i64, i64, i64, i32, i32, p, i64]
     lib.oracle_step.argtypes = [p, p, i64, i64, i64, ctypes.POINTER(_CRule), i32]
     lib.oracle_run.argtypes = [p, i64, i64, i64, ctypes.POINTER(_CRule), i32, i64]
-    for f in (lib.oracle_box_sums, lib.oracle_step, lib.oracle_run, lib.oracle_num_threads):
+    for f in (lib.oracle_box_sums, lib.oracle_cross_sums, lib.oracle_step, lib.oracle_run,
+              lib.oracle_num_threads):
         f.restype = ctypes.c_int
     return lib
 
@@ -96,13 +107,15 @@ def _grid(g: np.ndarray) -> np.ndarray:
     return g
 
 
-def box_sums(grid: np.ndarray, r: int, boundary: int = ZERO, lib=None) -> np.ndarray:
-    """L(y,x): state-1 cells in the (2r+1)^2 Moore box (centre included)."""
+def box_sums(grid: np.ndarray, r: int, boundary: int = ZERO, lib=None, nbhd: str = "M") -> np.ndarray:
+    """L(y,x): state-1 cells in the (2r+1)^2 Moore box (centre included), or with
+    nbhd "N" on the vertical plus the horizontal segment (Eq. 3, centre twice)."""
     lib = lib or load()
     g = _grid(grid)
     H, W = g.shape
     S = np.empty((H, W), dtype=np.int32)
-    rc = lib.oracle_box_sums(g.ctypes.data, H, W, W, int(r), int(boundary), S.ctypes.data, W)
+    fn = lib.oracle_cross_sums if nbhd == "N" else lib.oracle_box_sums
+    rc = fn(g.ctypes.data, H, W, W, int(r), int(boundary), S.ctypes.data, W)
     if rc != 0:
         raise ValueError(f"oracle_box_sums failed ({rc})")
     return S
@@ -113,7 +126,7 @@ def step(grid: np.ndarray, rule: Rule, boundary: int = ZERO, n_steps: int = 1, l
     lib = lib or load()
     g = _grid(grid).copy()
     H, W = g.shape
-    cr = _CRule(rule.r, rule.C, rule.M, rule.s1, rule.s2, rule.b1, rule.b2)
+    cr = _crule(rule)
     rc = lib.oracle_run(g.ctypes.data, H, W, W, ctypes.byref(cr), int(boundary), int(n_steps))
     if rc != 0:
         raise ValueError(f"oracle_run failed ({rc})")

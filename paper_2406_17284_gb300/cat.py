@@ -204,7 +204,8 @@ class Grid:
         self.rule = dict(rule)
         self.storage = int(storage)
         self.handle = cat_create_ex(self.H, self.W, make_rule(**{k: rule[k] for k in
-                                                                 ("r", "C", "M", "s1", "s2", "b1", "b2")}),
+                                                                 ("r", "C", "M", "s1", "s2", "b1", "b2")},
+                                                              nbhd=rule.get("nbhd", "M")),
                                     boundary, self.storage)
         try:
             cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage)

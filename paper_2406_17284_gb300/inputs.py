@@ -157,6 +157,19 @@ def scaled_rule(r: int, M: int = 1, C: int = 2) -> dict:
     return dict(r=r, C=C, M=M, s1=s1, s2=s2, b1=b1, b2=b2)
 
 
+def vn_scaled_rule_ranges(r: int) -> tuple[int, int, int, int]:
+    """The same percentages for the simplified von Neumann cross (vertical plus
+    horizontal segment of half-length r): n = 4r + 1 cells, the centre once."""
+    n = 4 * r + 1
+    rnd = lambda pct: (pct * n + 50) // 100  # noqa: E731
+    return rnd(34), rnd(58), rnd(34), rnd(45)
+
+
+def vn_scaled_rule(r: int, M: int = 1, C: int = 2) -> dict:
+    s1, s2, b1, b2 = vn_scaled_rule_ranges(r)
+    return dict(r=r, C=C, M=M, s1=s1, s2=s2, b1=b1, b2=b2, nbhd="N")
+
+
 CONWAY = dict(r=1, C=2, M=0, s1=2, s2=3, b1=3, b2=3)
 MULTISTATE_R10_C16 = dict(r=10, C=16, M=1, s1=150, s2=260, b1=150, b2=200)
 

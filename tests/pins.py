@@ -9,7 +9,9 @@ one pin).
 None of these re-types the oracle's loop: the box count is checked against the
 paper's own band-matrix product (Sec. IV, Eqs. 1-2, evaluated with numpy's
 integer matmul), a summed-area table, closed forms and textbook Game-of-Life
-behaviour; the transition against a table built from the rule's ranges.
+behaviour; the simplified von Neumann count against Eq. 3's products, its
+impulse response and closed forms; the transition against a table built from
+the rule's ranges.
 """
 from __future__ import annotations
 
@@ -49,6 +51,13 @@ def band_product_sums(grid: np.ndarray, r: int, periodic: bool) -> np.ndarray:
     return band(H, r, periodic) @ Hm         # Eq. 2: R = Pi x H
 
 
+def cross_product_sums(grid: np.ndarray, r: int, periodic: bool) -> np.ndarray:
+    """Eq. 3: R = Pi * Lambda + H with H = Lambda * Pi (vertical plus horizontal reduction)."""
+    lam = (grid == 1).astype(np.int64)
+    H, W = lam.shape
+    return band(H, r, periodic) @ lam + lam @ band(W, r, periodic)
+
+
 def sat_sums(grid: np.ndarray, r: int) -> np.ndarray:
     """Box sums with a zero boundary from a summed-area table."""
     lam = (grid == 1).astype(np.int64)
@@ -63,8 +72,13 @@ def sat_sums(grid: np.ndarray, r: int) -> np.ndarray:
 
 
 def table_transition(grid: np.ndarray, S: np.ndarray, rule: oracle.Rule) -> np.ndarray:
-    """Next states from box sums through lookup tables built from the rule's ranges."""
+    """Next states from box sums through lookup tables built from the rule's ranges.
+
+    A live cell's own state is in S once (Moore) or twice (Eq. 3); the rule's
+    count k keeps it once when M = 1 and drops it when M = 0.
+    """
     C, M = rule.C, rule.M
+    twice = 2 if rule.nbhd == "N" else 1
     n_max = int(S.max(initial=0)) + 2
     born = np.zeros(n_max + 1, dtype=np.uint8)
     born[max(rule.b1, 0):max(min(rule.b2, n_max) + 1, 0)] = 1
@@ -73,7 +87,7 @@ def table_transition(grid: np.ndarray, S: np.ndarray, rule: oracle.Rule) -> np.n
     out = np.zeros_like(grid)
     dead = grid == 0
     alive = grid == 1
-    k_alive = S - (1 if M == 0 else 0)
+    k_alive = S - (twice - M)
     out[dead] = born[np.clip(S[dead], 0, n_max)]
     surv = keep[np.clip(k_alive[alive], 0, n_max)]
     out[alive] = np.where(surv == 1, 1, 2 if C > 2 else 0)
@@ -254,6 +268,97 @@ def pin_middle_flag(lib):
         assert np.array_equal(oracle.step(g, m0, lib=lib), oracle.step(g, m1, lib=lib)), r
 
 
+# ------------------------------------------- simplified von Neumann (Eq. 3)
+def pin_vn_band_product(lib):
+    """Oracle cross sums == Pi x Lambda + Lambda x Pi (Eq. 3), both boundaries."""
+    rng = np.random.default_rng(12)
+    for (H, W) in [(1, 1), (3, 5), (7, 4), (12, 12), (17, 9), (20, 33)]:
+        for r in (0, 1, 2, 5, 8, 16):
+            g = rng.integers(0, 3, size=(H, W), dtype=np.uint8)
+            for periodic in (False, True):
+                got = oracle.box_sums(g, r, oracle.PERIODIC if periodic else oracle.ZERO, lib=lib, nbhd="N")
+                assert np.array_equal(got, cross_product_sums(g, r, periodic)), (H, W, r, periodic)
+
+
+def pin_vn_impulse(lib):
+    """A single live cell gives a cross of arm length r, 2 at its centre (on both segments)."""
+    for r in (1, 4, 16):
+        n = 2 * r + 7
+        g = np.zeros((n, n + 2), np.uint8)
+        cy, cx = n // 2, n // 2 + 1
+        g[cy, cx] = 1
+        want = np.zeros(g.shape, np.int32)
+        want[cy - r:cy + r + 1, cx] += 1
+        want[cy, cx - r:cx + r + 1] += 1
+        assert want[cy, cx] == 2
+        assert np.array_equal(oracle.box_sums(g, r, lib=lib, nbhd="N"), want), r
+
+
+def pin_vn_all_ones(lib):
+    """All-ones grid, zero halo: the clipped vertical plus the clipped horizontal segment length."""
+    for (H, W) in [(40, 40), (70, 45), (3, 100)]:
+        g = np.ones((H, W), np.uint8)
+        for r in (1, 9, 16):
+            y = np.arange(H)[:, None]
+            x = np.arange(W)[None, :]
+            want = (np.minimum(y + r, H - 1) - np.maximum(y - r, 0) + 1) + \
+                   (np.minimum(x + r, W - 1) - np.maximum(x - r, 0) + 1)
+            assert np.array_equal(oracle.box_sums(g, r, lib=lib, nbhd="N"), want), (H, W, r)
+    assert oracle.box_sums(np.ones((80, 80), np.uint8), 16, lib=lib, nbhd="N")[40, 40] == 66
+
+
+def pin_vn_transition_table(lib):
+    """Oracle steps (nbhd N) == table-driven transition on Eq. 3 sums, random rules incl. C > 2."""
+    rng = np.random.default_rng(6)
+    for trial in range(60):
+        H, W = int(rng.integers(1, 14)), int(rng.integers(1, 14))
+        r = int(rng.integers(1, 6))
+        C = int(rng.choice([2, 3, 16]))
+        M = int(rng.integers(0, 2))
+        n = 4 * r + 1
+        s1, s2 = sorted(int(v) for v in rng.integers(0, n + 1, 2))
+        b1, b2 = sorted(int(v) for v in rng.integers(1, n + 1, 2))
+        rule = oracle.Rule(r, C, M, s1, s2, b1, b2, "N")
+        g = rng.integers(0, C, size=(H, W), dtype=np.uint8)
+        periodic = bool(rng.integers(0, 2))
+        got = oracle.step(g, rule, oracle.PERIODIC if periodic else oracle.ZERO, lib=lib)
+        want = table_transition(g, cross_product_sums(g, r, periodic), rule)
+        assert np.array_equal(got, want), (trial, rule, periodic)
+
+
+def pin_vn_neighbour_count(lib):
+    """Counts from first principles: a lone live cell has 0 live neighbours (survives
+    S0..0 under M0, S1..1 under M1, dies under M0 S1..1); a dead cell with one live
+    cell on its cross (distance r along an axis) is born under B1..1, with one just
+    off the cross (diagonal) it is not."""
+    for r in (1, 3, 7):
+        n = 2 * r + 5
+        g = np.zeros((n, n), np.uint8)
+        c = n // 2
+        g[c, c] = 1
+        assert oracle.step(g, oracle.Rule(r, 2, 0, 0, 0, 9, 9, "N"), lib=lib)[c, c] == 1
+        assert oracle.step(g, oracle.Rule(r, 2, 1, 1, 1, 9, 9, "N"), lib=lib)[c, c] == 1
+        assert oracle.step(g, oracle.Rule(r, 2, 0, 1, 1, 9, 9, "N"), lib=lib)[c, c] == 0
+        for (dy, dx), born in [((0, r), 1), ((-r, 0), 1), ((1, 1), 0)]:
+            h = np.zeros((n, n), np.uint8)
+            h[c + dy, c + dx] = 1
+            assert oracle.step(h, oracle.Rule(r, 2, 0, 5, 5, 1, 1, "N"), lib=lib)[c, c] == born, (r, dy, dx)
+
+
+def pin_vn_symmetry(lib):
+    """The cross is symmetric (step(G^T) == step(G)^T) and the periodic step commutes
+    with cyclic shifts."""
+    g = inputs.bernoulli(37, 53, 0.45, 10)
+    rule = oracle.Rule(4, 2, 1, 5, 11, 5, 8, "N")
+    for b in (oracle.ZERO, oracle.PERIODIC):
+        assert np.array_equal(oracle.step(g.T.copy(), rule, b, lib=lib), oracle.step(g, rule, b, lib=lib).T), b
+    base = oracle.step(g, rule, oracle.PERIODIC, lib=lib)
+    for sy, sx in [(1, 0), (0, 1), (5, 17)]:
+        moved = oracle.step(np.roll(g, (sy, sx), (0, 1)), rule, oracle.PERIODIC, lib=lib)
+        assert np.array_equal(moved, np.roll(base, (sy, sx), (0, 1))), (sy, sx)
+
+
 ALL_PINS = [pin_band_product, pin_sat, pin_all_ones, pin_impulse, pin_transition_table,
             pin_conway, pin_all_zero, pin_decay_chain, pin_periodic_translation,
-            pin_transpose, pin_middle_flag]
+            pin_transpose, pin_middle_flag, pin_vn_band_product, pin_vn_impulse,
+            pin_vn_all_ones, pin_vn_transition_table, pin_vn_neighbour_count, pin_vn_symmetry]

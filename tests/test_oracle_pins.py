@@ -12,7 +12,7 @@ def test_pin(pin, oracle_mod):
 
 
 # Each planted mistake (see ORACLE_MUTATION in oracle/ltl_oracle.c) must be caught.
-@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6, 7])
 def test_pins_catch_planted_mistake(mutation, tmp_path):
     lib = oracle.load(oracle.compile_oracle(str(tmp_path), mutation=mutation))
     caught = []
