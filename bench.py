@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--multistate-size", type=int, default=49152, help="side of the multi-state grid (0: skip it)")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
     ap.add_argument("--no-bits", action="store_true", help="skip the one-bit-storage measurement")
+    ap.add_argument("--no-vn", action="store_true", help="skip the simplified von Neumann measurement")
     return ap.parse_args()
 
 
@@ -313,16 +314,9 @@ def measure_periodic(args, torch, cat, inputs, stream, radii=(1, 8, 16)):
     return out
 
 
-def measure_bits(args, torch, cat, inputs, stream, d_init, hbm, reps=3):
-    """One-bit storage: the headline's 16384^2 grid and 16 scaled rules stored 8 cells
-    per byte (FP8 operands), stepped round-robin over the radii like the headline, so
-    16 x 64 MiB pass between two steps of one grid (more than L2).  The algorithmic
-    traffic is 1/8 byte read + 1/8 byte written per cell update."""
-    n = args.size
-    grids = {r: cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype="fp8", storage=cat.STORE_BIT1)
-             for r in RADII}
-    for g in grids.values():
-        g.set_state(d_init)
+def measure_sweep(torch, cat, stream, grids, n, reps=3):
+    """Median device time per launch (ms) of each grid's step, the grids stepped
+    round-robin (radius order) reps times after one warm-up round."""
     for r in RADII:
         grids[r].step(1, stream)
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in RADII]
@@ -337,6 +331,37 @@ def measure_bits(args, torch, cat, inputs, stream, d_init, hbm, reps=3):
     for g in grids.values():
         assert g.status() == cat.CAT_OK
         g.close()
+    return per_r
+
+
+def measure_vn(args, torch, cat, inputs, stream, d_init, hbm):
+    """Simplified von Neumann neighbourhood (Eq. 3): the headline's 16384^2 grid with
+    the cross-scaled rules (n = 4r + 1, C2 M1), FP8 operands, uint8 storage (2 bytes
+    of algorithmic traffic per cell update), stepped round-robin over the radii."""
+    n = args.size
+    grids = {r: cat.Grid(n, n, inputs.vn_scaled_rule(r, M=1), kernel="tcgen05", dtype="fp8") for r in RADII}
+    for g in grids.values():
+        g.set_state(d_init)
+    per_r = measure_sweep(torch, cat, stream, grids, n)
+    ms = sum(per_r.values())
+    achieved = 2.0 * n * n * len(RADII) / (ms / 1000.0) / 1e9
+    return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, simplified von Neumann, fp8",
+            "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
+            "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
+            "bytes_per_cell": 2.0, "achieved_gbs": achieved, "hbm_frac": achieved / hbm}
+
+
+def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
+    """One-bit storage: the headline's 16384^2 grid and 16 scaled rules stored 8 cells
+    per byte (FP8 operands), stepped round-robin over the radii like the headline, so
+    16 x 64 MiB pass between two steps of one grid (more than L2).  The algorithmic
+    traffic is 1/8 byte read + 1/8 byte written per cell update."""
+    n = args.size
+    grids = {r: cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype="fp8", storage=cat.STORE_BIT1)
+             for r in RADII}
+    for g in grids.values():
+        g.set_state(d_init)
+    per_r = measure_sweep(torch, cat, stream, grids, n)
     ms = sum(per_r.values())
     achieved = 0.25 * n * n * len(RADII) / (ms / 1000.0) / 1e9
     return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, one bit per cell, fp8",
@@ -462,6 +487,9 @@ def run_cat(args, rank, world, local):
     bits = None
     if not args.no_bits and rank == 0:
         bits = measure_bits(args, torch, cat, inputs, stream, d_init, hbm)
+    vn = None
+    if not args.no_vn and rank == 0:
+        vn = measure_vn(args, torch, cat, inputs, stream, d_init, hbm)
 
     cpu = None
     if rank == 0:
@@ -493,6 +521,7 @@ def run_cat(args, rank, world, local):
             "multistate": multistate,
             "periodic": periodic,
             "bits": bits,
+            "von_neumann": vn,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,

@@ -211,6 +211,7 @@ class Grid:
             cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage)
         except Exception:
             cat_destroy(self.handle)
+            self.handle = None   # __del__ must not free it again
             raise
 
     def close(self):

@@ -107,7 +107,8 @@ int validate_rule(const cat_rule_t *r) {
   if (r->M != 0 && r->M != 1) return fail(CAT_ERR_INVALID_ARG, "M must be 0 or 1");
   if (r->s1 < 0 || r->s2 < 0 || r->b1 < 0 || r->b2 < 0)
     return fail(CAT_ERR_INVALID_ARG, "negative range bound");
-  if (r->nbhd != 'M') return fail(CAT_ERR_UNSUPPORTED, "only the Moore neighbourhood ('M') is served");
+  if (r->nbhd != 'M' && r->nbhd != 'N')
+    return fail(CAT_ERR_INVALID_ARG, "neighbourhood must be 'M' (Moore) or 'N' (simplified von Neumann)");
   return CAT_OK;
 }
 
@@ -117,9 +118,13 @@ RuleDev reduce_rule(const cat_rule_t &r) {
   d.r = r.r;
   d.C = r.C;
   d.M = r.M;
+  d.nbhd = r.nbhd == 'N' ? 1 : 0;
+  // a live cell's own state is in S once (Moore) or twice (the cross of
+  // Eq. 3); the rule's count keeps it once when M = 1, drops it when M = 0
+  const int own = (d.nbhd ? 2 : 1) - r.M;
   const int empty_lo = 1 << 24;
   if (r.s1 > r.s2) { d.s_lo = empty_lo; d.s_w = 0; }
-  else { d.s_lo = r.s1 + (r.M == 0 ? 1 : 0); d.s_w = r.s2 - r.s1; }
+  else { d.s_lo = r.s1 + own; d.s_w = r.s2 - r.s1; }
   if (r.b1 > r.b2) { d.b_lo = empty_lo; d.b_w = 0; }
   else { d.b_lo = r.b1; d.b_w = r.b2 - r.b1; }
   return d;
@@ -181,8 +186,9 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     cat::TcParams p;
     memset(&p, 0, sizeof(p));
     p.ox = p.oy = h->ghost;
+    const bool vn = h->rule.nbhd == 'N';
     const bool bits = h->storage == CAT_STORE_BIT1;
-    const bool sw = !bits && short_window(h);
+    const bool sw = !vn && !bits && short_window(h);
     p.map_in_a = h->maps[in][sw ? 3 : 0];
     p.map_in_b = h->maps[in][sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
@@ -198,7 +204,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.timeout_ns = h->timeout_ns;
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
-    e = cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
+    e = vn ? cat::vn_launch(p, grid, s) : cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
   } else {
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
     cat::SimpleParams p;
@@ -451,6 +457,8 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   if (storage == CAT_STORE_BIT1 && rule->C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
   if (storage == CAT_STORE_BIT1 && boundary != CAT_BOUNDARY_ZERO)
     return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
+  if (storage == CAT_STORE_BIT1 && rule->nbhd != 'M')
+    return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served for the Moore neighbourhood only");
   cat_instance *h = new (std::nothrow) cat_instance();
   if (!h) return fail(CAT_ERR_OOM, "host allocation failed");
   if ((rc = device_info(&h->dev))) { delete h; return rc; }
@@ -462,6 +470,10 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   h->pitch = storage == CAT_STORE_BIT1 ? round_up((W + 7) / 8, 16) : round_up(W + 2 * h->ghost, 16);
   h->rule = *rule;
   h->rd = reduce_rule(*rule);
+  if (rule->nbhd == 'N' && rule->C > 2) {  // the cross with C > 2 runs on the CUDA-core stencil
+    h->kernel = CAT_KERNEL_STENCIL;
+    h->dtype = CAT_DTYPE_INT8;
+  }
   const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
   cudaError_t e = cudaMalloc(&h->buf[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
@@ -488,7 +500,8 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
   if (steps_per_launch != 1) return fail(CAT_ERR_UNSUPPORTED, "only one step per launch is served yet");
-  if (kernel == CAT_KERNEL_AUTO) kernel = CAT_KERNEL_TCGEN05;
+  const bool vn = h->rule.nbhd == 'N';
+  if (kernel == CAT_KERNEL_AUTO) kernel = vn && h->rule.C > 2 ? CAT_KERNEL_STENCIL : CAT_KERNEL_TCGEN05;
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
   if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
     return fail(CAT_ERR_UNSUPPORTED, dtype == CAT_DTYPE_INT8 ? "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC"
@@ -498,6 +511,14 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
   if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
     return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
+  if (vn) {
+    if (kernel == CAT_KERNEL_MMA_SYNC)
+      return fail(CAT_ERR_UNSUPPORTED, "the simplified von Neumann neighbourhood is served by the tcgen05 and stencil kernels");
+    if (kernel == CAT_KERNEL_TCGEN05 && (dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2))
+      return fail(CAT_ERR_UNSUPPORTED, "the tcgen05 von Neumann kernel serves FP8 operands and two-state rules");
+    if (storage == CAT_STORE_BIT1)
+      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served for the Moore neighbourhood only");
+  }
   if (storage == CAT_STORE_BIT1) {
     if (h->rule.C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
@@ -561,9 +582,10 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   }
   if (count == 0 || n_steps == 0) return CAT_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  bool all_tc = true;   // zero boundary, uint8 storage: other instances step one by one
+  bool all_tc = true;   // Moore, zero boundary, uint8 storage: other instances step one by one
   for (int32_t i = 0; i < count; ++i) {
-    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8;
+    all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8 &&
+              hs[i]->rule.nbhd == 'M';
     if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
       return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
     if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)

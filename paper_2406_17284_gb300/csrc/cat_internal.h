@@ -17,7 +17,7 @@ namespace cat {
 struct RuleDev {
   int32_t r, C, M;
   int32_t s_lo, s_w, b_lo, b_w;
-  int32_t pad;
+  int32_t nbhd;  // 0: Moore box; 1: simplified von Neumann cross (centre counted twice)
 };
 
 // One instance of a batched launch (global memory, read by the kernel).
@@ -82,6 +82,8 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 // bits: one bit per cell (FP8, C = 2, single instance): map_in_a is the 48 x
 // 160-byte window map and map_out / map_ctr the 16 x 128-byte tile maps.
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits, int grid, cudaStream_t s);
+// Simplified von Neumann neighbourhood (FP8, C = 2, single instance).
+cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s);
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
 size_t tc_smem_bytes(int dt, bool encode, bool sw);
 

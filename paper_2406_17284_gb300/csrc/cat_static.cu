@@ -92,6 +92,7 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
       return err(CAT_ERR_INVALID_ARG, "grid %lld: buffers must be 16-byte aligned", i);
     int rc = cat::host_validate_rule(&g.rule);
     if (rc) return rc;
+    if (g.rule.nbhd != 'M') return err(CAT_ERR_UNSUPPORTED, "grid %lld: the static batch serves the Moore neighbourhood", i);
     encode |= g.rule.C > 2;
     n_tiles += ((g.H + 127) / 128) * ((g.W + 127) / 128);
   }

@@ -2,6 +2,8 @@
 // paper compares against, Sec. V-A Table V): a CTA stages its (B + 2r)^2
 // window of states in shared memory and every thread sums the (2r+1)^2 box of
 // each of its cells directly, then applies the LTL rule.  O(r^2) work per cell.
+// With the simplified von Neumann neighbourhood (Eq. 3) it sums the vertical
+// and the horizontal segment instead (the centre on both), O(r) per cell.
 #include "cat_internal.h"
 
 namespace cat {
@@ -38,9 +40,13 @@ __global__ void __launch_bounds__(kThreads) smem_stencil_kernel(const SimplePara
     const int gy = y0 + ty, gx = x0 + tx;
     if (gy >= p.H || gx >= p.W) continue;
     int s = 0;
-    for (int dy = 0; dy <= 2 * r; ++dy) {
-      const uint8_t *row = win + (ty + dy) * SW + tx;
-      for (int dx = 0; dx <= 2 * r; ++dx) s += row[dx];
+    if (p.rule.nbhd) {
+      for (int d = 0; d <= 2 * r; ++d) s += win[(ty + d) * SW + tx + r] + win[(ty + r) * SW + tx + d];
+    } else {
+      for (int dy = 0; dy <= 2 * r; ++dy) {
+        const uint8_t *row = win + (ty + dy) * SW + tx;
+        for (int dx = 0; dx <= 2 * r; ++dx) s += row[dx];
+      }
     }
     if (p.sums) p.sums[(int64_t)gy * p.sums_ld + gx] = s;
     else p.out[(int64_t)gy * p.pitch + gx] = (uint8_t)next_state(s, ctr[ty * BX + tx], p.rule);

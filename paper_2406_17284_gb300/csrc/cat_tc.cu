@@ -867,6 +867,278 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   }
 }
 
+// ---------------------------------------------------------------------------
+// Simplified von Neumann neighbourhood (Eq. 3): R = Pi x Lambda + H with
+// H = Lambda x Pi, the sums over the vertical and the horizontal segment of
+// half-length r through each cell (the centre lies on both).  Both products
+// accumulate into one tensor-memory region, so nothing leaves the tensor
+// memory between them:
+//   V[y][x] = sum_y' band[y][y'] X[y'][x]   A = the band in tensor memory;
+//             B = X as an MN-major operand: the 128-column x 160-row box at
+//             (x0, y0 - 16), 128B swizzle, K = y' along its rows;
+//   H[y][x] = sum_x' X[y][x'] band[x'][x]   A = rows 16..143 of the haloed
+//             160 x 160 window (K-major, K = x'); B = the band as a K-major
+//             operand in shared memory (row x holds band[.][x]).
+// X is read as raw 0/1 bytes (e4m3 2^-9) and the bands hold e4m3 1.0, so the
+// f16 accumulator holds R * 2^-9, exact (R <= 2(2r+1) = 66).  Rows 16..143
+// of the column box are the centre tile: the epilogue overwrites them with
+// the next states, warp 2 stores them, and the stage is then free.
+namespace vn {
+constexpr int NS = 4;                                // stages: window + column box
+constexpr int kRegions = 3;                          // accumulators of 128 columns
+constexpr uint32_t kColOff = kWin * kWin;            // column box, after boxes a (128 B) and b (32 B) x 160 rows
+constexpr uint32_t kCtrOff = kColOff + 16 * 128;     // centre tile: column-box rows 16..143
+constexpr uint32_t kStage = kColOff + kTile * kWin;  // 46080 bytes, all delivered by the three loads
+constexpr uint32_t kBandB = NS * kStage;             // horizontal band, K-major, 128 rows x 160
+constexpr uint32_t kBars = kBandB + kTile * kWin;
+constexpr uint32_t kDyn = kBars + 512 + 1024;
+constexpr uint32_t kBandCol = kRegions * kTile;      // vertical band (A operand), 40 columns
+static_assert(kColOff % 1024 == 0 && kCtrOff % 1024 == 0 && kStage % 1024 == 0 && kBandB % 1024 == 0,
+              "swizzled operands start on 1024-byte boundaries");
+static_assert(kDyn <= 232448, "shared memory budget");
+static_assert(kBandCol + 40 <= kTmemCols, "tensor memory budget");
+static_assert(kRegions <= kMaxRegions, "barrier arrays");
+
+// V: five K-steps of 32 rows of the column box (4096 bytes each).
+template <int J = 0>
+__device__ __forceinline__ void vertical_mma(uint32_t d, uint32_t band, uint64_t col0, uint32_t idesc) {
+  if constexpr (J < 5) {
+    mma_f8f6f4_ts(d, band + 8 * J, col0 + (uint64_t)((4096 * J) >> 4), idesc, J > 0);
+    vertical_mma<J + 1>(d, band, col0, idesc);
+  }
+}
+
+// H: five K-steps of 32 columns of the window rows against the band.
+template <int J = 0>
+__device__ __forceinline__ void horizontal_mma(uint32_t d, const OpDesc &win, const OpDesc &band, uint32_t idesc) {
+  if constexpr (J < 5) {
+    mma_f8f6f4(d, op_desc_k<kWin, 1, J>(win), op_desc_k<kTile, 1, J>(band), idesc, 1);
+    horizontal_mma<J + 1>(d, win, band, idesc);
+  }
+}
+}  // namespace vn
+
+// One step (or the counts R) of a single instance, FP8 operands, two-state
+// rules.  Warps: 0 loads, 1 allocates tensor memory and issues the MMAs, 2
+// stores, 4..11 build the two bands, 12..27 evaluate the rule.
+__global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_constant__ TcParams p) {
+  constexpr float kScale = 1.0f / 512.0f;            // accumulator = R * kScale
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars *bars = reinterpret_cast<Bars *>(smem + vn::kBars);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int first, n_my;
+  my_range<false>(p, first, n_my);
+  int32_t *err0 = p.err;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < vn::NS; ++i) {
+      mbar_init(&bars->x_full[i], 1);
+      mbar_init(&bars->x_empty[i], 1);            // the store thread, once the stage is stored
+      mbar_init(&bars->out_full[i], kEpiWarps);
+    }
+    for (int i = 0; i < vn::kRegions; ++i) {
+      mbar_init(&bars->d2_full[i], 1);
+      mbar_init(&bars->tmem_empty[i], kEpiWarps);
+    }
+    mbar_init(&bars->band_ready, kCvtWarps);
+    mbar_init(&bars->mma_done[0], 1);
+    mbar_init(&bars->never, 1);
+    bars->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&bars->tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  const uint32_t s_base = smem_u32(smem);
+
+  if (warp == 0) {
+    // --------------------------------------------------------------- loads
+    if (lane == 0) {
+      int issued = 0;
+      TileSeq<false> seq(p, first);
+      for (int j = 0; j < n_my; ++j, seq.next(p)) {
+        const int s = j % vn::NS;
+        const Tile t = seq.get(p);
+        if (j == 0) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
+        if (!mbar_wait(&bars->x_empty[s], ((j / vn::NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
+        uint8_t *st = smem + s * vn::kStage;
+        mbar_arrive_expect_tx(&bars->x_full[s], vn::kStage);
+        tma_load_2d(st, t.in_a, t.tx0 - 16, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(st + kWin * 128, t.in_b, t.tx0 + 112, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(st + vn::kColOff, t.in_a, t.tx0, t.ty0 - 16, &bars->x_full[s]);
+        issued = j + 1;
+      }
+      volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
+      for (int j = issued - 1; j >= 0 && j >= issued - vn::NS; --j)
+        if (!mbar_wait(&bars->x_full[j % vn::NS], (j / vn::NS) & 1, &no_abort, p.timeout_ns)) set_abort(bars, err0, 2);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc_v = idesc_f16acc(128, kTile) | (1u << 16);  // B (column box) MN-major
+      const uint32_t idesc_h = idesc_f16acc(128, kTile);
+      const uint32_t band_a = tmem + vn::kBandCol;
+      const OpDesc band_b = op_descs(s_base + vn::kBandB);
+      bool ok = true;
+      if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
+        ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
+        if (!ok) set_abort(bars, err0, 3);
+      }
+      if (ok && !(ok = mbar_wait(&bars->band_ready, 0, &bars->abort, p.timeout_ns))) set_abort(bars, err0, 4);
+      for (int j = 0; ok && j < n_my; ++j) {
+        const int reg = j % vn::kRegions, s = j % vn::NS;
+        if (!(ok = mbar_wait(&bars->tmem_empty[reg], ((j / vn::kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 5); break; }
+        if (!(ok = mbar_wait(&bars->x_full[s], (j / vn::NS) & 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 6); break; }
+        tc_fence_after();
+        const uint32_t st = s_base + s * vn::kStage;
+        const uint32_t d = tmem + reg * kTile;
+        vn::vertical_mma(d, band_a, smem_desc(st + vn::kColOff, 1024, 1024, kSwizzle128B), idesc_v);
+        const OpDesc win{smem_desc(st + 16 * 128, 16, 1024, kSwizzle128B), smem_desc(st + 16 * 32, 16, 256, kSwizzle32B)};
+        vn::horizontal_mma(d, win, band_b, idesc_h);
+        mma_commit(&bars->d2_full[reg]);
+      }
+      mma_commit(&bars->mma_done[0]);  // drain before the tensor memory is freed
+      volatile int no_abort = 0;
+      if (!mbar_wait(&bars->mma_done[0], 0, &no_abort, p.timeout_ns)) set_abort(bars, err0, 12);
+    }
+  } else if (warp == 2) {
+    // -------------------------------------------------------------- stores
+    if (lane == 0) {
+      TileSeq<false> seq(p, first);
+      for (int j = 0; j < n_my; ++j, seq.next(p)) {
+        const int s = j % vn::NS;
+        const Tile t = seq.get(p);
+        if (!mbar_wait(&bars->out_full[s], (j / vn::NS) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
+        if (!p.sums) {
+          tma_store_2d(t.out, t.tx0, t.ty0, smem + s * vn::kStage + vn::kCtrOff);
+          bulk_commit();
+          bulk_wait_read<0>();          // the store has read the stage
+        }
+        mbar_arrive(&bars->x_empty[s]);
+      }
+      bulk_wait<0>();                   // all writes complete before the CTA exits
+    }
+  } else if (warp == 3) {
+    // idle
+  } else if (warp < 4 + kCvtWarps) {
+    // --------------------------------------------------------------- bands
+    const int q = warp & 3, kq = (warp - 4) >> 2, r = p.rule.r;
+    {  // vertical band: lane m = output row y, K = window row y', one iff |y' - 16 - y| <= r
+      const int m = 32 * q + lane;
+      const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
+      for (int c = kq; c < 5; c += 2) {
+        uint32_t v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          uint32_t w = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int d = 4 * (8 * c + i) + b - m - 16;
+            if (d >= -r && d <= r) w |= 0x38u << (8 * b);
+          }
+          v[i] = w;
+        }
+        tmem_st8(tmem + la + vn::kBandCol + 8 * c, v);
+      }
+      tmem_wait_st();
+    }
+    // horizontal band: row x (N), K = window column x', one iff |x' - 16 - x| <= r
+    for (int i = threadIdx.x - 128; i < kTile * 10; i += kCvtThreads) {
+      const int c = i / kTile, x = i - c * kTile;
+      uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const int d = 16 * c + b - 16 - x;
+        if (d >= -r && d <= r) w[b >> 2] |= 0x38u << (8 * (b & 3));
+      }
+      *reinterpret_cast<uint4 *>(smem + vn::kBandB + op_off(kTile, 1, x, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars->band_ready);
+  } else {
+    // ------------------------------------------------ epilogue warps (12 .. 27)
+    const int q = warp & 3;
+    const int kq = (warp - 4 - kCvtWarps) >> 2;      // 0..3: which warp of the quarter
+    const int y = 32 * q + lane;                     // TMEM lane = output row y
+    const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
+    uint32_t off_c[2];                               // column chunks kq and kq + 4 of row y
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = kq + 4 * c;
+      off_c[c] = y * 128 + (((cc ^ y) & 7) << 4);
+    }
+    bool ok = true;
+    const HalfRule hr = make_half_rule(p.rule, kScale);
+    TileSeq<false> seq(p, first);
+    for (int j = 0; ok && j < n_my; ++j, seq.next(p)) {
+      const int reg = j % vn::kRegions, s = j % vn::NS;
+      const Tile t = seq.get(p);
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / vn::kRegions) & 1, bars, p.timeout_ns))) break;
+      tc_fence_after();
+      uint32_t v[2][8];                              // R * scale as f16 pairs
+      {
+        const uint32_t treg = tmem + lane_addr + reg * kTile;
+        tmem_ld16_pack16(treg + 16 * kq, v[0]);
+        tmem_ld16_pack16(treg + 16 * (kq + 4), v[1]);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->tmem_empty[reg]);
+      }
+      // the stage's loads completed before its MMAs; waiting on the same phase
+      // (still current: the stage is freed only after this tile's store) makes
+      // the centre tile visible to these threads
+      if (!(ok = warp_wait(&bars->x_full[s], (j / vn::NS) & 1, bars, p.timeout_ns))) break;
+      uint8_t *ctr = smem + s * vn::kStage + vn::kCtrOff;
+      if (!p.sums) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint4 *cell = reinterpret_cast<uint4 *>(ctr + off_c[c]);
+          const uint4 cv = *cell;
+          uint4 ov;
+          ov.x = rule4_binary_h(v[c][0], v[c][1], cv.x, hr);
+          ov.y = rule4_binary_h(v[c][2], v[c][3], cv.y, hr);
+          ov.z = rule4_binary_h(v[c][4], v[c][5], cv.z, hr);
+          ov.w = rule4_binary_h(v[c][6], v[c][7], cv.w, hr);
+          *cell = ov;
+        }
+      } else {  // the counts R of Eq. 3
+        const int gy = t.y0 + y;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int cc = kq + 4 * c;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint32_t h2 = v[c][i >> 1];
+            const float sv = (i & 1) ? half_hi(h2) : half_lo(h2);
+            const int gx = t.x0 + 16 * cc + i;
+            if (gy < t.H && gx < t.W) p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(sv * (1.0f / kScale));
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->out_full[s]);
+    }
+    if (!ok) set_abort(bars, err0, 8);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 }  // namespace tc
 
 // dt follows cat.h: 1 = FP16, 2 = FP8 e4m3.
@@ -901,6 +1173,20 @@ cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits
   if (encode) return launch_one<1, true, false>(p, grid, s);
   if (sw) return launch_one<1, false, false, true>(p, grid, s);
   return launch_one<1, false, false>(p, grid, s);
+}
+
+// Simplified von Neumann neighbourhood: FP8, two-state rules, single instance
+// (map_in_a / map_in_b: the 128 x 160 and 32 x 160 window maps; map_out: the
+// 128 x 128 tile map of the output buffer).
+cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_vn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::vn::kDyn);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  tc::ltl_vn_kernel<<<grid, tc::kThreads, tc::vn::kDyn, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s) {

@@ -50,7 +50,7 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
         (10, 10, cat.make_rule(1, 1, 0, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 2, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 0, -1, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
-        (10, 10, cat.make_rule(1, 2, 0, 2, 3, 3, 3, nbhd="N"), 0, cat.CAT_ERR_UNSUPPORTED),
+        (10, 10, cat.make_rule(1, 2, 0, 2, 3, 3, 3, nbhd="X"), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, good, -1, cat.CAT_ERR_INVALID_ARG),   # boundaries: 0 zero, 1 periodic
         (10, 10, good, 7, cat.CAT_ERR_INVALID_ARG),
         (1 << 40, 1 << 20, good, 0, cat.CAT_ERR_INVALID_ARG),
@@ -60,6 +60,16 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
         assert rc == want, (H, W, b, rc, lib.cat_last_error())
         assert out.value is None
         assert lib.cat_last_error()
+    # one-bit storage: two-state Moore rules with the zero boundary; unknown storage codes
+    vn = cat.make_rule(1, 2, 0, 2, 3, 3, 3, nbhd="N")
+    multi = cat.make_rule(1, 3, 0, 2, 3, 3, 3)
+    for rule, b, st, want in [(vn, 0, cat.STORE_BIT1, cat.CAT_ERR_UNSUPPORTED),
+                              (multi, 0, cat.STORE_BIT1, cat.CAT_ERR_UNSUPPORTED),
+                              (good, 1, cat.STORE_BIT1, cat.CAT_ERR_UNSUPPORTED),
+                              (good, 0, 5, cat.CAT_ERR_INVALID_ARG)]:
+        rc = lib.cat_create_ex(10, 10, ctypes.byref(rule), b, st, ctypes.byref(out))
+        assert rc == want, (rule.nbhd, b, st, rc, lib.cat_last_error())
+        assert out.value is None
 
 
 def test_null_handles_rejected(lib):
