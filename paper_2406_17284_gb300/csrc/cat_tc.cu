@@ -171,15 +171,19 @@ struct Layout {
                 "swizzled operands start on 1024-byte boundaries");
 };
 
+constexpr int kMaxStages = 6;
+
 struct Bars {
-  uint64_t x_full[4], x_empty[4];
-  uint64_t c_full[4], out_full[4];
+  uint64_t x_full[kMaxStages], x_empty[kMaxStages];
+  uint64_t c_full[kMaxStages], out_full[kMaxStages];
   uint64_t d1_full[kMaxRegions], d2_full[kMaxRegions], tmem_empty[kMaxRegions];
   uint64_t h_full[3], enc_full[3], band_ready;
   uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
 };
+
+static_assert(sizeof(Bars) <= 512, "the barrier block fits its reserved 512 bytes");
 
 __device__ __forceinline__ void set_abort(Bars *b, int32_t *err, int where) {
   b->abort = 1;
@@ -475,6 +479,8 @@ __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 *
 template <int DT, bool ENC, bool BATCH, bool SW, bool BITS>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
   static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
+  static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
+                Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
   using L = Layout<DT, ENC, SW, BITS>;
   using G = Geo<SW>;
   constexpr int kRegions = G::kRegions;
@@ -874,30 +880,38 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 // accumulate into one tensor-memory region, so nothing leaves the tensor
 // memory between them:
 //   V[y][x] = sum_y' band[y][y'] X[y'][x]   A = the band in tensor memory;
-//             B = X as an MN-major operand: the 128-column x 160-row box at
-//             (x0, y0 - 16), 128B swizzle, K = y' along its rows;
-//   H[y][x] = sum_x' X[y][x'] band[x'][x]   A = rows 16..143 of the haloed
-//             160 x 160 window (K-major, K = x'); B = the band as a K-major
-//             operand in shared memory (row x holds band[.][x]).
-// X is read as raw 0/1 bytes (e4m3 2^-9) and the bands hold e4m3 1.0, so the
-// f16 accumulator holds R * 2^-9, exact (R <= 2(2r+1) = 66).  Rows 16..143
-// of the column box are the centre tile: the epilogue overwrites them with
-// the next states, warp 2 stores them, and the stage is then free.
+//             B = X as an MN-major operand: the centre box, 128 columns x 160
+//             rows at (x0, y0 - 16), 128B swizzle, K = y' along its rows;
+//   H[y][x] = sum_x' X[y][x'] band[x'][x]   A = rows 16..143 of three boxes
+//             side by side in K (x' = x0 - 32 ..): the left box (32 columns,
+//             32B swizzle), the centre box and the right box (32 columns),
+//             K-major, one 32-column K-step of the left and the right box
+//             each; B = the band as a K-major operand in shared memory, cut
+//             the same way (row x holds band[.][x]).
+// A stage is 192 x 160 bytes, the fewest whole boxes that hold the halo and
+// the centre box once.  X is read as raw 0/1 bytes (e4m3 2^-9) and the bands
+// hold e4m3 1.0, so the f16 accumulator holds R * 2^-9, exact (R <= 2(2r+1)
+// = 66).  Rows 16..143 of the centre box are the centre tile: the epilogue
+// overwrites them with the next states, warp 2 stores them, and the stage is
+// then free.
 namespace vn {
-constexpr int NS = 4;                                // stages: window + column box
+constexpr int NS = 6;                                // stages
 constexpr int kRegions = 3;                          // accumulators of 128 columns
-constexpr uint32_t kColOff = kWin * kWin;            // column box, after boxes a (128 B) and b (32 B) x 160 rows
-constexpr uint32_t kCtrOff = kColOff + 16 * 128;     // centre tile: column-box rows 16..143
-constexpr uint32_t kStage = kColOff + kTile * kWin;  // 46080 bytes, all delivered by the three loads
-constexpr uint32_t kBandB = NS * kStage;             // horizontal band, K-major, 128 rows x 160
-constexpr uint32_t kBars = kBandB + kTile * kWin;
+constexpr uint32_t kLeft = kTile * kWin;             // 20480: left box, 32 B x 160 rows (centre box at 0)
+constexpr uint32_t kRight = kLeft + 32 * kWin;       // 25600: right box, 32 B x 160 rows
+constexpr uint32_t kStage = kRight + 32 * kWin;      // 30720 bytes, all delivered by the three loads
+constexpr uint32_t kCtrOff = 16 * 128;               // centre tile: centre-box rows 16..143
+constexpr uint32_t kBandC = NS * kStage;             // horizontal band: centre piece, 128 rows x 128 B
+constexpr uint32_t kBandL = kBandC + kTile * 128;    // left piece, 128 rows x 32 B
+constexpr uint32_t kBandR = kBandL + kTile * 32;     // right piece, 128 rows x 32 B
+constexpr uint32_t kBars = kBandR + kTile * 32;
 constexpr uint32_t kDyn = kBars + 512 + 1024;
 constexpr uint32_t kBandCol = kRegions * kTile;      // vertical band (A operand), 40 columns
-static_assert(kColOff % 1024 == 0 && kCtrOff % 1024 == 0 && kStage % 1024 == 0 && kBandB % 1024 == 0,
-              "swizzled operands start on 1024-byte boundaries");
+static_assert(kLeft % 1024 == 0 && kStage % 1024 == 0 && kBandC % 1024 == 0 && kRight % 256 == 0 &&
+              kBandL % 256 == 0 && kBandR % 256 == 0, "swizzle atoms stay aligned");
 static_assert(kDyn <= 232448, "shared memory budget");
 static_assert(kBandCol + 40 <= kTmemCols, "tensor memory budget");
-static_assert(kRegions <= kMaxRegions, "barrier arrays");
+static_assert(kRegions <= kMaxRegions && NS <= kMaxStages, "barrier arrays");
 
 // V: five K-steps of 32 rows of the column box (4096 bytes each).
 template <int J = 0>
@@ -908,13 +922,22 @@ __device__ __forceinline__ void vertical_mma(uint32_t d, uint32_t band, uint64_t
   }
 }
 
-// H: five K-steps of 32 columns of the window rows against the band.
-template <int J = 0>
-__device__ __forceinline__ void horizontal_mma(uint32_t d, const OpDesc &win, const OpDesc &band, uint32_t idesc) {
-  if constexpr (J < 5) {
-    mma_f8f6f4(d, op_desc_k<kWin, 1, J>(win), op_desc_k<kTile, 1, J>(band), idesc, 1);
-    horizontal_mma<J + 1>(d, win, band, idesc);
-  }
+// H: the left box, four K-steps of 32 columns of the centre box, the right
+// box, each against its piece of the band (descriptors of rows 16.. of the
+// stage, and of the band pieces).
+__device__ __forceinline__ void horizontal_mma(uint32_t d, uint64_t a_left, uint64_t a_centre, uint64_t a_right,
+                                               uint64_t b_left, uint64_t b_centre, uint64_t b_right, uint32_t idesc) {
+  mma_f8f6f4(d, a_left, b_left, idesc, 1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) mma_f8f6f4(d, a_centre + 2 * j, b_centre + 2 * j, idesc, 1);   // +32 bytes of K
+  mma_f8f6f4(d, a_right, b_right, idesc, 1);
+}
+
+// Byte offset of (row, kb) in a K-major operand piece of 128B (w = 128) or
+// 32B (w = 32) swizzle, rows at w bytes.
+__device__ __forceinline__ uint32_t piece_off(int w, int row, int kb) {
+  if (w == 128) return row * 128 + ((((kb >> 4) ^ row) & 7) << 4) + (kb & 15);
+  return row * 32 + ((((kb >> 4) ^ (row >> 2)) & 1) << 4) + (kb & 15);
 }
 }  // namespace vn
 
@@ -969,9 +992,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_consta
         if (!mbar_wait(&bars->x_empty[s], ((j / vn::NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *st = smem + s * vn::kStage;
         mbar_arrive_expect_tx(&bars->x_full[s], vn::kStage);
-        tma_load_2d(st, t.in_a, t.tx0 - 16, t.ty0 - 16, &bars->x_full[s]);
-        tma_load_2d(st + kWin * 128, t.in_b, t.tx0 + 112, t.ty0 - 16, &bars->x_full[s]);
-        tma_load_2d(st + vn::kColOff, t.in_a, t.tx0, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(st, t.in_a, t.tx0, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(st + vn::kLeft, t.in_b, t.tx0 - 32, t.ty0 - 16, &bars->x_full[s]);
+        tma_load_2d(st + vn::kRight, t.in_b, t.tx0 + 128, t.ty0 - 16, &bars->x_full[s]);
         issued = j + 1;
       }
       volatile int no_abort = 0;  // drain: the last load issued into each stage has landed
@@ -984,7 +1007,9 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_consta
       const uint32_t idesc_v = idesc_f16acc(128, kTile) | (1u << 16);  // B (column box) MN-major
       const uint32_t idesc_h = idesc_f16acc(128, kTile);
       const uint32_t band_a = tmem + vn::kBandCol;
-      const OpDesc band_b = op_descs(s_base + vn::kBandB);
+      const uint64_t b_left = smem_desc(s_base + vn::kBandL, 16, 256, kSwizzle32B);
+      const uint64_t b_centre = smem_desc(s_base + vn::kBandC, 16, 1024, kSwizzle128B);
+      const uint64_t b_right = smem_desc(s_base + vn::kBandR, 16, 256, kSwizzle32B);
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
         ok = mbar_wait(&bars->never, 0, &bars->abort, p.timeout_ns);
@@ -998,9 +1023,10 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_consta
         tc_fence_after();
         const uint32_t st = s_base + s * vn::kStage;
         const uint32_t d = tmem + reg * kTile;
-        vn::vertical_mma(d, band_a, smem_desc(st + vn::kColOff, 1024, 1024, kSwizzle128B), idesc_v);
-        const OpDesc win{smem_desc(st + 16 * 128, 16, 1024, kSwizzle128B), smem_desc(st + 16 * 32, 16, 256, kSwizzle32B)};
-        vn::horizontal_mma(d, win, band_b, idesc_h);
+        vn::vertical_mma(d, band_a, smem_desc(st, 1024, 1024, kSwizzle128B), idesc_v);
+        vn::horizontal_mma(d, smem_desc(st + vn::kLeft + 16 * 32, 16, 256, kSwizzle32B),
+                           smem_desc(st + 16 * 128, 16, 1024, kSwizzle128B),
+                           smem_desc(st + vn::kRight + 16 * 32, 16, 256, kSwizzle32B), b_left, b_centre, b_right, idesc_h);
         mma_commit(&bars->d2_full[reg]);
       }
       mma_commit(&bars->mma_done[0]);  // drain before the tensor memory is freed
@@ -1048,16 +1074,21 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_consta
       }
       tmem_wait_st();
     }
-    // horizontal band: row x (N), K = window column x', one iff |x' - 16 - x| <= r
-    for (int i = threadIdx.x - 128; i < kTile * 10; i += kCvtThreads) {
+    // horizontal band: row x (N), K = column x' = x0 - 32 + k of the three
+    // boxes side by side, one iff |x' - x0 - x| = |k - 32 - x| <= r; 16-byte
+    // chunk c of K: 0, 1 in the left piece, 2..9 the centre, 10, 11 the right
+    for (int i = threadIdx.x - 128; i < kTile * 12; i += kCvtThreads) {
       const int c = i / kTile, x = i - c * kTile;
       uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
-        const int d = 16 * c + b - 16 - x;
+        const int d = 16 * c + b - 32 - x;
         if (d >= -r && d <= r) w[b >> 2] |= 0x38u << (8 * (b & 3));
       }
-      *reinterpret_cast<uint4 *>(smem + vn::kBandB + op_off(kTile, 1, x, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+      const uint32_t off = c < 2 ? vn::kBandL + vn::piece_off(32, x, 16 * c)
+                         : c < 10 ? vn::kBandC + vn::piece_off(128, x, 16 * (c - 2))
+                                  : vn::kBandR + vn::piece_off(32, x, 16 * (c - 10));
+      *reinterpret_cast<uint4 *>(smem + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     fence_proxy_async_smem();
     tc_fence_before();
