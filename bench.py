@@ -137,16 +137,18 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(dtype: str, cells: int):
-    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
-    scaled to `cells`; None when the kernel source changed since the capture."""
+def recorded_traffic(kernel: str, cells: int):
+    """DRAM bytes per launch from the committed ncu capture of `kernel` ("fp8", "fp16",
+    "vn", "bits"; profiles/traffic.json), scaled to `cells`; None when the kernel source
+    changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
         if rec.get("kernel_source_sha") != kernel_source_sha():
             return None
-        cap = rec["captures"][dtype]
-        return cap["traffic_bytes_per_launch"] * cells / (rec["grid"][0] * rec["grid"][1])
+        cap = rec["captures"][kernel]
+        grid = cap.get("grid", rec.get("grid"))
+        return cap["traffic_bytes_per_launch"] * cells / (grid[0] * grid[1])
     except Exception:
         return None
 
@@ -348,7 +350,8 @@ def measure_vn(args, torch, cat, inputs, stream, d_init, hbm):
     return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, simplified von Neumann, fp8",
             "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
             "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
-            "bytes_per_cell": 2.0, "achieved_gbs": achieved, "hbm_frac": achieved / hbm}
+            "bytes_per_cell": 2.0, "achieved_gbs": achieved, "hbm_frac": achieved / hbm,
+            "traffic_bytes_per_launch": recorded_traffic("vn", n * n), "kernel": "ltl_vn_kernel"}
 
 
 def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
@@ -367,7 +370,8 @@ def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
     return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, one bit per cell, fp8",
             "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
             "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
-            "bytes_per_cell": 0.25, "achieved_gbs": achieved, "hbm_frac": achieved / hbm}
+            "bytes_per_cell": 0.25, "achieved_gbs": achieved, "hbm_frac": achieved / hbm,
+            "traffic_bytes_per_launch": recorded_traffic("bits", n * n), "kernel": "ltl_bits_kernel"}
 
 
 def run_cat(args, rank, world, local):

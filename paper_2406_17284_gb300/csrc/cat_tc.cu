@@ -477,7 +477,7 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
 template <int DT, bool ENC, bool BATCH, bool SW, bool BITS>
-__global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
+__device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
   static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
                 Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
@@ -873,6 +873,17 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
   }
 }
 
+template <int DT, bool ENC, bool BATCH, bool SW>
+__global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<DT, ENC, BATCH, SW, false>(p);
+}
+
+// One bit per cell: the same body under its own name, so that a profiler can
+// single it out.
+__global__ void __launch_bounds__(kThreads, 1) ltl_bits_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, true, false, false, true>(p);
+}
+
 // ---------------------------------------------------------------------------
 // Simplified von Neumann neighbourhood (Eq. 3): R = Pi x Lambda + H with
 // H = Lambda x Pi, the sums over the vertical and the horizontal segment of
@@ -1183,13 +1194,15 @@ template <int DT, bool ENC, bool BATCH, bool SW = false, bool BITS = false>
 static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
   static bool configured = false;
   const size_t smem = tc::Layout<DT, ENC, SW, BITS>::kDyn;
+  void (*kern)(TcParams);
+  if constexpr (BITS) kern = tc::ltl_bits_kernel;
+  else kern = tc::ltl_tc_kernel<DT, ENC, BATCH, SW>;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc::ltl_tc_kernel<DT, ENC, BATCH, SW, BITS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_tc_kernel<DT, ENC, BATCH, SW, BITS><<<grid, tc::kThreads, smem, s>>>(p);
+  kern<<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
