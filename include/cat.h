@@ -57,8 +57,17 @@ extern "C" {
  *   M      1: the centre cell counts towards k; 0: it does not
  *   s1,s2  survival range for state-1 cells (inclusive; s1 > s2 means empty)
  *   b1,b2  birth range for state-0 cells (inclusive; b1 > b2 means empty)
- *   nbhd   'M' (Moore).  The von Neumann variants of Eq. 3 are not served.
- * Negative range bounds are rejected.                                        */
+ *   nbhd   'M': Moore box of (2r+1)^2 cells (Eqs. 1-2);
+ *          'N': simplified von Neumann cross (Eq. 3, R = Pi*Lambda + H): the
+ *          vertical and the horizontal segment of half-length r, 4r + 1 cells.
+ *          R holds the centre twice; k = R - 2c for M = 0 and R - c for M = 1,
+ *          so k counts the live neighbours (plus the cell itself when M = 1)
+ *          as with the Moore box.  Served by TCGEN05 with FP8 operands for
+ *          C = 2 and by STENCIL for every C (CAT_KERNEL_AUTO picks the
+ *          stencil when C > 2); not by MMA_SYNC, BIT1 storage or
+ *          cat_batch_step_static.
+ * Negative range bounds are rejected; nbhd other than 'M' / 'N' is
+ * INVALID_ARG.                                                              */
 typedef struct cat_rule {
   int32_t r, C, M, s1, s2, b1, b2;
   int32_t nbhd;
@@ -173,9 +182,11 @@ CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);
  * replayed from a CUDA graph cached for this handle list.                   */
 CAT_API int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream);
 
-/* Debug/verification: writes the box counts L(y,x) of the current state,
- * computed by the selected kernel's band products, to dst (device memory,
- * int32, row stride ld >= W elements).  Does not advance the state.         */
+/* Debug/verification: writes the counts of the current state, computed by
+ * the selected kernel's band products, to dst (device memory, int32, row
+ * stride ld >= W elements): the Moore box count L(y,x) (centre once), or for
+ * nbhd 'N' the cross count R(y,x) of Eq. 3 (centre twice).  Does not advance
+ * the state.                                                                */
 CAT_API int cat_box_sums(cat_handle_t h, int32_t *dst, int64_t ld, void *stream);
 
 /* Synchronises `stream` and reports device-side failures of this instance's
