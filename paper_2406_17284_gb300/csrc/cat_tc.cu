@@ -230,10 +230,6 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
 // shifted copies of n land on disjoint bit ranges).
 __device__ __forceinline__ uint32_t bits4_to_bytes(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
 
-// Four bytes 0/1 -> four bits (byte b to bit b): the multiplier moves byte b's
-// low bit to bit 24 + b and every other product term below bit 24 or above 31.
-__device__ __forceinline__ uint32_t bytes_to_bits4(uint32_t w) { return (w * 0x01020408u) >> 24 & 0xFu; }
-
 // Unpacks a bit-packed window stage (160 rows of 48 bytes, window cell x' at
 // bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell.
 // One item is half a row (80 cells, 16-cell chunks 5h .. 5h+4): three aligned
@@ -349,6 +345,33 @@ __device__ __forceinline__ uint32_t rule4_binary_h(uint32_t s01, uint32_t s23, u
   uint32_t neg;   // bytes 1, 3 of t01 and 5, 7 of t23 (the sign bytes), sign-replicated
   asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(neg) : "r"(h2_bits(t01)), "r"(h2_bits(t23)));
   return ~neg & 0x01010101u;
+}
+
+// Out-of-range flags (product signs) of four cells as a nibble, cell k in bit
+// k: the sign bytes (1 and 3) of two half2 products side by side, and their
+// top bits gathered by one multiply (every partial product lands on its own
+// bit, so nothing carries into bits 28..31).
+__device__ __forceinline__ uint32_t sign_nibble(__half2 t01, __half2 t23) {
+  const uint32_t x = __byte_perm(h2_bits(t01), h2_bits(t23), 0x7531) & 0x80808080u;
+  return (x * 0x00204081u) >> 28;
+}
+
+// Next states of 16 cells of a two-state rule as bits (lowest cell lowest),
+// from their counts as f16 pairs (v[i]: cells 2i, 2i + 1) and their current
+// states as bits.  Every cell gets both range tests, (s - lo)(hi - s) >= 0 as
+// in rule4_binary_h, on the FMA pipe; one three-input logic op then picks the
+// survival test for live cells and the birth test for dead ones.  Cheaper in
+// integer instructions than expanding the bits to bytes for rule4_binary_h.
+__device__ __forceinline__ uint32_t rule16_bits(const uint32_t (&v)[8], uint32_t c, const HalfRule &h) {
+  const __half2 sl = as_h2(h.sl2), sh = as_h2(h.sh2), bl = as_h2(h.bl2), bh = as_h2(h.bh2);
+  uint32_t out_s = 0, out_b = 0;  // out of the survival / birth range
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 s0 = as_h2(v[2 * i]), s1 = as_h2(v[2 * i + 1]);
+    out_s |= sign_nibble(__hmul2(__hsub2(s0, sl), __hsub2(sh, s0)), __hmul2(__hsub2(s1, sl), __hsub2(sh, s1))) << (4 * i);
+    out_b |= sign_nibble(__hmul2(__hsub2(s0, bl), __hsub2(bh, s0)), __hmul2(__hsub2(s1, bl), __hsub2(bh, s1))) << (4 * i);
+  }
+  return ~((c & out_s) | (~c & out_b)) & 0xFFFFu;
 }
 
 // 0x01 in each byte of w that is not zero, else 0x00 (no carry between bytes:
@@ -809,11 +832,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           for (int c = 0; c < 2; ++c) {
             const int cc = kq + 4 * c;
             uint16_t *cellp = reinterpret_cast<uint16_t *>(ring + y * 16 + 2 * cc);
-            const uint32_t b = *cellp;
-            uint32_t nb = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              nb |= bytes_to_bits4(rule4_binary_h(v[c][2 * i], v[c][2 * i + 1], bits4_to_bytes(b >> (4 * i)), hr)) << (4 * i);
+            uint32_t nb = rule16_bits(v[c], *cellp, hr);
             const int lim = t.W - (t.x0 + 16 * cc);
             if (lim < 16) nb &= lim > 0 ? (1u << lim) - 1u : 0u;
             *cellp = (uint16_t)nb;
