@@ -446,19 +446,39 @@ def run_cat(args, rank, world, local):
     alg_bytes = 2.0 * n * n  # read + write of one uint8 state per cell
     achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
 
-    # ---- e2e: same metric through the C ABI from pinned host memory
+    # ---- e2e: same metric through the C ABI from pinned host memory.  Every
+    # step of every grid copies its input in (cat_set_state), steps it and
+    # copies the result out (cat_get_state), on three streams so that the
+    # host-to-device copy of one grid, the step of another and the
+    # device-to-host copy of a third overlap (a grid's next input waits for
+    # its previous result to be read out; results alternate between two
+    # pinned buffers).
     pin_in = torch.from_numpy(host).pin_memory()
-    pin_out = torch.empty_like(pin_in).pin_memory()
+    pin_out = [torch.empty_like(pin_in).pin_memory() for _ in range(2)]
     e2e_steps = max(1, min(args.steps, 3))
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    read_out = {r: None for r in RADII}
     torch.cuda.synchronize()
     te0 = time.perf_counter()
+    k = 0
     for _ in range(e2e_steps):
         for r in RADII:
             g = grids[r]
-            cat.cat_set_state(g.handle, pin_in.data_ptr(), n, False, stream)
+            if read_out[r] is not None:
+                s_in.wait_event(read_out[r])
+            cat.cat_set_state(g.handle, pin_in.data_ptr(), n, False, s_in)
+            copied = torch.cuda.Event()
+            copied.record(s_in)
+            stream.wait_event(copied)
             g.step(1, stream)
-            cat.cat_get_state(g.handle, pin_out.data_ptr(), n, False, stream)
-        stream.synchronize()
+            stepped = torch.cuda.Event()
+            stepped.record(stream)
+            s_out.wait_event(stepped)
+            cat.cat_get_state(g.handle, pin_out[k & 1].data_ptr(), n, False, s_out)
+            k += 1
+            read_out[r] = torch.cuda.Event()
+            read_out[r].record(s_out)
+    torch.cuda.synchronize()
     te = (time.perf_counter() - te0) / e2e_steps
     e2e_value = cells_per_step * world / te
 

@@ -535,7 +535,11 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
 }
 
 static int copy2d(void *dst, int64_t dpitch, const void *src, int64_t spitch, int64_t W, int64_t H, cudaStream_t s) {
-  CAT_CUDA(cudaMemcpy2DAsync(dst, (size_t)dpitch, src, (size_t)spitch, (size_t)W, (size_t)H, cudaMemcpyDefault, s));
+  if (dpitch == W && spitch == W) {  // both sides contiguous: one linear copy
+    CAT_CUDA(cudaMemcpyAsync(dst, src, (size_t)(W * H), cudaMemcpyDefault, s));
+  } else {
+    CAT_CUDA(cudaMemcpy2DAsync(dst, (size_t)dpitch, src, (size_t)spitch, (size_t)W, (size_t)H, cudaMemcpyDefault, s));
+  }
   return CAT_OK;
 }
 
