@@ -347,7 +347,17 @@ def measure_vn(args, torch, cat, inputs, stream, d_init, hbm):
     per_r = measure_sweep(torch, cat, stream, grids, n)
     ms = sum(per_r.values())
     achieved = 2.0 * n * n * len(RADII) / (ms / 1000.0) / 1e9
+    paper = {}   # the paper-style FP16 fragment kernel on the same grid (Eq. 3 as printed)
+    if not args.no_compare:
+        for r in (1, 8, 16):
+            g = cat.Grid(n, n, inputs.vn_scaled_rule(r, M=1), kernel="mma_sync", dtype="fp16")
+            g.set_state(d_init)
+            g.step(1, stream)
+            t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
+            paper[str(r)] = n * n / (statistics.median(t) / 1000.0)
+            g.close()
     return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, simplified von Neumann, fp8",
+            "paper_fp16_fragments_cell_updates_per_s": paper,
             "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
             "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
             "bytes_per_cell": 2.0, "achieved_gbs": achieved, "hbm_frac": achieved / hbm,

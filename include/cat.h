@@ -63,9 +63,9 @@ extern "C" {
  *          R holds the centre twice; k = R - 2c for M = 0 and R - c for M = 1,
  *          so k counts the live neighbours (plus the cell itself when M = 1)
  *          as with the Moore box.  Served by TCGEN05 with FP8 operands for
- *          C = 2 and by STENCIL for every C (CAT_KERNEL_AUTO picks the
- *          stencil when C > 2); not by MMA_SYNC, BIT1 storage or
- *          cat_batch_step_static.
+ *          C = 2, by MMA_SYNC with FP16 operands and by STENCIL for every C
+ *          (CAT_KERNEL_AUTO picks the stencil when C > 2); not by MMA_SYNC
+ *          with INT8 operands, BIT1 storage or cat_batch_step_static.
  * Negative range bounds are rejected; nbhd other than 'M' / 'N' is
  * INVALID_ARG.                                                              */
 typedef struct cat_rule {

@@ -512,8 +512,8 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
     return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
   if (vn) {
-    if (kernel == CAT_KERNEL_MMA_SYNC)
-      return fail(CAT_ERR_UNSUPPORTED, "the simplified von Neumann neighbourhood is served by the tcgen05 and stencil kernels");
+    if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16)
+      return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves the simplified von Neumann neighbourhood with FP16 operands");
     if (kernel == CAT_KERNEL_TCGEN05 && (dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2))
       return fail(CAT_ERR_UNSUPPORTED, "the tcgen05 von Neumann kernel serves FP8 operands and two-state rules");
     if (storage == CAT_STORE_BIT1)

@@ -12,6 +12,9 @@
 // Step 2 (Eq. 5, with F^H in all three terms, as in Alg. 1):
 // F^R_{i,j} = pi3 F^H_{i-1,j} + pi2 F^H_{i,j} + pi1 F^H_{i+1,j}.
 // Then every thread applies the LTL rule to its cells (Alg. 1, last loop).
+// Simplified von Neumann neighbourhood (Eq. 3, R = Pi x Lambda + H), FP16 path:
+// step 2 takes the Lambda fragments instead of F^H and starts from the
+// accumulator F^H_{i,j} instead of zero (the MMA's C operand).
 //
 // FP16 path: nvcuda::wmma 16x16x16 with FP16 accumulation.  Every partial sum
 // is an integer <= (2r+1)^2 <= 1089 < 2^11, so FP16 holds it exactly (Sec. V-A).
@@ -89,14 +92,24 @@ __global__ void __launch_bounds__(kThreads) cat_wmma_f16_kernel(const SimplePara
   for (int k = warp; k < FH * FW; k += kThreads / 32) {
     const int i = k / FW + 1, j = k - (i - 1) * FW;
     wmma::fragment<wmma::accumulator, 16, 16, 16, half> F;
-    wmma::fill_fragment(F, __float2half(0.0f));
     wmma::fragment<wmma::matrix_a, 16, 16, 16, half, wmma::row_major> A;
     wmma::fragment<wmma::matrix_b, 16, 16, 16, half, wmma::row_major> B;
+    if (R.nbhd) {  // Eq. 3: C = F^H_{i,j}, B = Lambda fragments
+      wmma::load_matrix_sync(F, qh + (16 * i) * TW + 16 * j, TW, wmma::mem_row_major);
 #pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-      wmma::load_matrix_sync(A, pis[1 - d], 16);  // pi3 for i-1, pi2 for i, pi1 for i+1
-      wmma::load_matrix_sync(B, qh + (16 * (i + d)) * TW + 16 * j, TW);
-      wmma::mma_sync(F, A, B, F);
+      for (int d = -1; d <= 1; ++d) {
+        wmma::load_matrix_sync(A, pis[1 - d], 16);
+        wmma::load_matrix_sync(B, lam + (16 * (i + d)) * WW + 16 * (j + 1), WW);
+        wmma::mma_sync(F, A, B, F);
+      }
+    } else {
+      wmma::fill_fragment(F, __float2half(0.0f));
+#pragma unroll
+      for (int d = -1; d <= 1; ++d) {
+        wmma::load_matrix_sync(A, pis[1 - d], 16);  // pi3 for i-1, pi2 for i, pi1 for i+1
+        wmma::load_matrix_sync(B, qh + (16 * (i + d)) * TW + 16 * j, TW);
+        wmma::mma_sync(F, A, B, F);
+      }
     }
     wmma::store_matrix_sync(qr + (16 * (i - 1)) * TW + 16 * j, F, TW, wmma::mem_row_major);
   }

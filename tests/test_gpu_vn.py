@@ -3,7 +3,9 @@
 The count of a cell is the sum over the vertical and the horizontal segment of
 half-length r through it, the centre counted on both (R = Pi x Lambda + H).
 The tcgen05 kernel accumulates both band products in one tensor-memory
-region (FP8 operands, two-state rules); the CUDA-core stencil serves every C.
+region (FP8 operands, two-state rules); the paper-style fragment kernel (FP16
+wmma) starts its second step from F^H as the MMA's C operand; the CUDA-core
+stencil serves every C.
 Both are compared with the oracle on counts and on whole steps, at sizes that
 span several tiles with ragged tails, on the degenerate shapes, with the
 periodic boundary, and on the full 16384^2 launch through sampled windows.
@@ -18,7 +20,7 @@ from paper_2406_17284_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [("tcgen05", "fp8"), ("stencil", "auto")]
+KERNELS = [("tcgen05", "fp8"), ("mma_sync", "fp16"), ("stencil", "auto")]
 KIDS = [f"{k}-{d}" for k, d in KERNELS]
 
 
@@ -134,6 +136,7 @@ def test_multistate_on_the_stencil(cat):
         want = oracle.step(grid, orule(rule), n_steps=5)
         assert_same(run(cat, "auto", "auto", grid, rule, 5), want, f"C={C} auto")
         assert_same(run(cat, "stencil", "auto", grid, rule, 5), want, f"C={C} stencil")
+        assert_same(run(cat, "mma_sync", "fp16", grid, rule, 5), want, f"C={C} mma_sync")
         with pytest.raises(cat.CatError) as e:
             cat.Grid(64, 64, rule, kernel="tcgen05", dtype="fp8")
         assert e.value.code == cat.CAT_ERR_UNSUPPORTED
@@ -141,7 +144,7 @@ def test_multistate_on_the_stencil(cat):
 
 def test_unsupported_combinations(cat):
     rule = inputs.vn_scaled_rule(4)
-    for kernel, dtype in (("mma_sync", "fp16"), ("mma_sync", "int8"), ("tcgen05", "fp16")):
+    for kernel, dtype in (("mma_sync", "int8"), ("tcgen05", "fp16")):
         with pytest.raises(cat.CatError) as e:
             cat.Grid(64, 64, rule, kernel=kernel, dtype=dtype)
         assert e.value.code == cat.CAT_ERR_UNSUPPORTED, (kernel, dtype)
