@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-boundary measurement")
     ap.add_argument("--no-bits", action="store_true", help="skip the one-bit-storage measurement")
     ap.add_argument("--no-vn", action="store_true", help="skip the simplified von Neumann measurement")
+    ap.add_argument("--no-multistep", action="store_true", help="skip the several-steps-per-launch measurement")
     return ap.parse_args()
 
 
@@ -364,6 +365,24 @@ def measure_vn(args, torch, cat, inputs, stream, d_init, hbm):
             "traffic_bytes_per_launch": recorded_traffic("vn", n * n), "kernel": "ltl_vn_kernel"}
 
 
+def measure_multistep(torch, cat, inputs, stream, steps=64):
+    """Small single grids (L2-resident), the scaled rule r = 4 (FP8): `steps` steps with
+    one launch per step (cat_step, k = 1) and with all of them in one cooperative
+    launch (k = steps, CTAs meeting on a grid barrier between steps)."""
+    out = {"workload": f"{steps} steps of one grid, scaled rule r=4 C2 M1, fp8"}
+    for n in (512, 1024, 2048):
+        init = torch.from_numpy(inputs.bernoulli(n, n, 0.5, SEED + n)).cuda()
+        for k in (1, steps):
+            g = cat.Grid(n, n, inputs.scaled_rule(4, M=1), kernel="tcgen05", dtype="fp8", steps_per_launch=k)
+            g.set_state(init)
+            g.step(steps, stream)
+            t = time_launches(torch, lambda: g.step(steps, stream), 3, stream)
+            assert g.status() == cat.CAT_OK
+            out[f"{n}x{n}_k{k}_cell_updates_per_s"] = n * n * steps / (statistics.median(t) / 1000.0)
+            g.close()
+    return out
+
+
 def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
     """One-bit storage: the headline's 16384^2 grid and 16 scaled rules stored 8 cells
     per byte (FP8 operands), stepped round-robin over the radii like the headline, so
@@ -524,6 +543,9 @@ def run_cat(args, rank, world, local):
     vn = None
     if not args.no_vn and rank == 0:
         vn = measure_vn(args, torch, cat, inputs, stream, d_init, hbm)
+    multistep = None
+    if not args.no_multistep and rank == 0:
+        multistep = measure_multistep(torch, cat, inputs, stream)
 
     cpu = None
     if rank == 0:
@@ -556,6 +578,7 @@ def run_cat(args, rank, world, local):
             "periodic": periodic,
             "bits": bits,
             "von_neumann": vn,
+            "multistep": multistep,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,

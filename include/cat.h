@@ -145,7 +145,13 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).
  * CAT_STORE_BIT1 needs C = 2, the zero boundary, TCGEN05 and FP8_E4M3.
- * steps_per_launch must be 1.  Errors: INVALID_ARG for unknown values,
+ * steps_per_launch = k > 1 makes cat_step run k steps per kernel launch: one
+ * cooperative launch (all CTAs resident, one per SM) whose CTAs meet on a
+ * grid-wide barrier between steps, so small grids stop paying a launch per
+ * step; served by TCGEN05 for the Moore neighbourhood with the zero boundary
+ * (any dtype, storage or C).  A launch that gives up on a barrier wait sets
+ * the status word like any other bounded wait; cat_status then also resets
+ * the barrier counter.  Errors: INVALID_ARG for unknown values,
  * UNSUPPORTED for combinations this build does not serve (e.g. TCGEN05 +
  * INT8: sm_103a has no tcgen05 kind::i8), OOM, CUDA.  After INVALID_ARG,
  * UNSUPPORTED or OOM the instance keeps its previous options and state.     */

@@ -199,7 +199,7 @@ class Grid:
     """One LTL instance: owns a cat handle; state in/out as numpy or torch tensors."""
 
     def __init__(self, H: int, W: int, rule: dict, kernel: str = "tcgen05", dtype: str = "fp8",
-                 boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8):
+                 boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8, steps_per_launch: int = 1):
         self.H, self.W = int(H), int(W)
         self.rule = dict(rule)
         self.storage = int(storage)
@@ -208,7 +208,7 @@ class Grid:
                                                               nbhd=rule.get("nbhd", "M")),
                                     boundary, self.storage)
         try:
-            cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage)
+            cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage, steps_per_launch)
         except Exception:
             cat_destroy(self.handle)
             self.handle = None   # __del__ must not free it again

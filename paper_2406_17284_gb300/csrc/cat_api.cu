@@ -94,6 +94,8 @@ struct cat_instance {
   DeviceInfo dev;
   int32_t inject = 0;
   uint64_t timeout_ns = 2000000000ull;
+  int32_t steps_per_launch = 1;  // > 1: cooperative launches of several steps
+  uint32_t gbar_count = 0;       // arrivals on the grid-barrier counter (d_err[1]) so far
   // grid cell (0, 0) of buffer b (past the ghost frame when there is one)
   uint8_t *origin(int b) const { return buf[b] + ghost * pitch + ghost; }
 };
@@ -175,8 +177,10 @@ bool short_window(const cat_instance *h) {
   return h->kernel == CAT_KERNEL_TCGEN05 && h->dtype == CAT_DTYPE_FP8_E4M3 && h->rule.C == 2 && h->rule.r <= 7;
 }
 
-// One step of instance h from buffer `in` into buffer 1 - in (or box sums into `sums`).
-int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStream_t s) {
+// n_steps steps of instance h from buffer `in` (into buffer 1 - in after an
+// odd count), or the box sums of buffer `in` into `sums`.  n_steps > 1 is one
+// cooperative launch of the tcgen05 Moore kernel (zero boundary).
+int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStream_t s, int n_steps = 1) {
   cudaError_t e;
   if (h->kernel == CAT_KERNEL_TCGEN05) {
     if (h->ghost) {  // periodic: refresh the input's ghost frame first
@@ -193,6 +197,15 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.map_in_b = h->maps[in][sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
     p.map_ctr = h->maps[in][2];
+    p.n_steps = n_steps;
+    if (n_steps > 1) {  // odd steps: buffers swapped; the grid barrier counter sits after the status word
+      p.map2_in_a = h->maps[1 - in][sw ? 3 : 0];
+      p.map2_in_b = h->maps[1 - in][sw ? 4 : 1];
+      p.map2_out = h->maps[in][2];
+      p.map2_ctr = h->maps[1 - in][2];
+      p.gbar = reinterpret_cast<uint32_t *>(h->d_err) + 1;
+      p.gbar_base = h->gbar_count;
+    }
     p.H = (int32_t)h->H;
     p.W = (int32_t)h->W;
     p.tiles_x = (int32_t)((h->W + 127) / 128);
@@ -205,6 +218,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
     e = vn ? cat::vn_launch(p, grid, s) : cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
+    if (e == cudaSuccess && n_steps > 1) h->gbar_count += (uint32_t)grid * (uint32_t)(n_steps - 1);
   } else {
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
     cat::SimpleParams p;
@@ -499,7 +513,6 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (dtype < CAT_DTYPE_AUTO || dtype > CAT_DTYPE_FP4_E2M1) return fail(CAT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
   if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
-  if (steps_per_launch != 1) return fail(CAT_ERR_UNSUPPORTED, "only one step per launch is served yet");
   const bool vn = h->rule.nbhd == 'N';
   if (kernel == CAT_KERNEL_AUTO) kernel = vn && h->rule.C > 2 ? CAT_KERNEL_STENCIL : CAT_KERNEL_TCGEN05;
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
@@ -525,12 +538,15 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
     if (kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3)
       return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 operands");
   }
+  if (steps_per_launch > 1 && (kernel != CAT_KERNEL_TCGEN05 || vn || h->ghost))
+    return fail(CAT_ERR_UNSUPPORTED, "several steps per launch are served by the tcgen05 Moore kernel with the zero boundary");
   if (storage != h->storage) {
     int rc = change_storage(h, storage);
     if (rc) return rc;
   }
   h->kernel = kernel;
   h->dtype = dtype;
+  h->steps_per_launch = steps_per_launch;
   return CAT_OK;
 }
 
@@ -569,10 +585,12 @@ int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch) {
 int cat_step(cat_handle_t h, int64_t n_steps, void *stream) {
   if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
   if (n_steps < 0) return fail(CAT_ERR_INVALID_ARG, "n_steps < 0");
-  for (int64_t t = 0; t < n_steps; ++t) {
-    int rc = launch_step(h, h->cur, nullptr, 0, (cudaStream_t)stream);
+  for (int64_t t = 0; t < n_steps;) {
+    const int m = (int)std::min<int64_t>(h->steps_per_launch, n_steps - t);
+    int rc = launch_step(h, h->cur, nullptr, 0, (cudaStream_t)stream, m);
     if (rc) return rc;
-    h->cur ^= 1;
+    h->cur ^= m & 1;
+    t += m;
   }
   return CAT_OK;
 }
@@ -658,7 +676,10 @@ int cat_status(cat_handle_t h, void *stream) {
   int32_t v = 0;
   CAT_CUDA(cudaMemcpy(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost));
   if (v != 0) {
-    CAT_CUDA(cudaMemset(h->d_err, 0, sizeof(v)));
+    // the status word and the grid-barrier counter (a launch that gave up
+    // left it short of its last target)
+    CAT_CUDA(cudaMemset(h->d_err, 0, 2 * sizeof(v)));
+    h->gbar_count = 0;
     return fail(CAT_ERR_TIMEOUT, "a device-side wait timed out (code 0x%x)", v);
   }
   return CAT_OK;

@@ -59,6 +59,13 @@ struct TcParams {
   int32_t parity;   // batch mode: step index & 1
   const BatchInst *binst;
   const BatchTile *btiles;
+  // several steps in one cooperative launch (single instance, n_steps > 1):
+  // odd steps read and write through the second set of maps (buffers
+  // swapped), and all CTAs meet on a grid barrier between steps
+  CUtensorMap map2_in_a, map2_in_b, map2_out, map2_ctr;
+  int32_t n_steps;       // steps in this launch (1 unless cooperative)
+  uint32_t gbar_base;    // barrier counter value when the launch starts
+  uint32_t *gbar;        // barrier counter (global memory)
 };
 
 // Parameters of the warp-level kernels (mma.sync fragments, CUDA-core stencil).

@@ -426,21 +426,34 @@ __device__ __forceinline__ void my_range(const TcParams &p, int &first, int &cou
 
 // Walks this CTA's tiles in order: tile j of the work-list chunk (batch) or
 // tile id blockIdx + j * gridDim (single instance), whose (tx, ty) advances
-// by a fixed step without a division.
-template <bool BATCH>
+// by a fixed step without a division.  MS: a single instance stepped several
+// times in one launch walks its `per` tiles once per step; odd steps use the
+// second set of maps.
+template <bool BATCH, bool MS = false>
 struct TileSeq {
   int first, j, tx, ty, sx, sy;
-  __device__ __forceinline__ TileSeq(const TcParams &p, int first_) : first(first_), j(0), tx(0), ty(0), sx(0), sy(0) {
-    if constexpr (!BATCH) {
-      ty = (int)blockIdx.x / p.tiles_x;
-      tx = (int)blockIdx.x - ty * p.tiles_x;
-      sy = (int)gridDim.x / p.tiles_x;
-      sx = (int)gridDim.x - sy * p.tiles_x;
-    }
+  int k, per, step;   // single instance: tile k of this CTA's `per` tiles in step `step`
+  __device__ __forceinline__ TileSeq(const TcParams &p, int first_, int per_ = 0)
+      : first(first_), j(0), tx(0), ty(0), sx(0), sy(0), k(0), per(per_), step(0) {
+    if constexpr (!BATCH) start(p);
+  }
+  __device__ __forceinline__ void start(const TcParams &p) {
+    ty = (int)blockIdx.x / p.tiles_x;
+    tx = (int)blockIdx.x - ty * p.tiles_x;
+    sy = (int)gridDim.x / p.tiles_x;
+    sx = (int)gridDim.x - sy * p.tiles_x;
   }
   __device__ __forceinline__ void next(const TcParams &p) {
     ++j;
     if constexpr (!BATCH) {
+      if constexpr (MS) {
+        if (++k == per) {   // next step: back to this CTA's first tile
+          k = 0;
+          ++step;
+          start(p);
+          return;
+        }
+      }
       tx += sx;
       ty += sy;
       if (tx >= p.tiles_x) { tx -= p.tiles_x; ++ty; }
@@ -465,10 +478,11 @@ struct TileSeq {
       t.R = I->rule;
       t.err = I->err;
     } else {
-      t.in_a = &p.map_in_a;
-      t.in_b = &p.map_in_b;
-      t.out = &p.map_out;
-      t.ctr = &p.map_ctr;
+      const bool odd = MS && (step & 1);
+      t.in_a = odd ? &p.map2_in_a : &p.map_in_a;
+      t.in_b = odd ? &p.map2_in_b : &p.map_in_b;
+      t.out = odd ? &p.map2_out : &p.map_out;
+      t.ctr = odd ? &p.map2_ctr : &p.map_ctr;
       t.x0 = tx * kTile;
       t.y0 = ty * kTile;
       t.tx0 = t.x0 + p.ox;
@@ -499,8 +513,9 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 // exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
-template <int DT, bool ENC, bool BATCH, bool SW, bool BITS>
+template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS>
 __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
+  static_assert(!MS || !BATCH, "several steps per launch serve single instances");
   static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
   static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
                 Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
@@ -522,6 +537,11 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   my_range<BATCH>(p, first, n_my);
   int32_t *err0 = n_my > 0 ? tile_err<BATCH>(p, first, 0) : (BATCH ? nullptr : p.err);
   const int r0 = n_my > 0 ? tile_rule<BATCH>(p, first, 0).r : 1;
+  // several steps per launch (single instance): every role walks n_my tiles
+  // per step; the loads of step s >= 1 wait on the grid barrier that all CTAs
+  // reach once their step s - 1 stores have completed
+  const int n_steps = MS ? (p.n_steps > 1 ? p.n_steps : 1) : 1;
+  const int n_all = MS ? n_my * n_steps : n_my;
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
@@ -561,8 +581,8 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   const uint32_t s_base = smem_u32(smem);
 
   // The convert warps encode window j into buffer j % NE once pass 1 of tile
-  // j - NE has read that buffer: the first NE windows before the tile loop,
-  // window j + NE right after converting D1 of tile j.
+  // j - NE has read that buffer (at the start of the loop iteration of tile
+  // j - NE + 1, or of the step's first tile when window j opens a step).
   auto encode = [&](int j, int tid, int nthr) -> bool {
     const int s = j % L::NS, e = j % L::NE;
     if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
@@ -580,11 +600,20 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     // Streams the haloed windows into NS stages (freed by pass 1 or the encoder).
     if (lane == 0) {
       int issued = 0;
-      TileSeq<BATCH> seq(p, first);
-      for (int j = 0; j < n_my; ++j, seq.next(p)) {
+      TileSeq<BATCH, MS> seq(p, first, n_my);
+      for (int j = 0; j < n_all; ++j, seq.next(p)) {
         const int s = j % NS;
         const Tile t = seq.get(p);
-        if (j == 0 || BATCH) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
+        if constexpr (MS) {
+          if (seq.k == 0 && seq.step > 0) {   // step `step` reads what every CTA stored in step - 1
+            if (!gbar_wait(p.gbar, p.gbar_base + (uint32_t)seq.step * gridDim.x, &bars->abort, p.timeout_ns)) {
+              set_abort(bars, err0, 14);
+              break;
+            }
+            fence_proxy_async_global();
+          }
+        }
+        if ((MS ? seq.k == 0 : j == 0) || BATCH) { prefetch_tmap(t.in_a); prefetch_tmap(t.in_b); }
         if (!mbar_wait(&bars->x_empty[s], ((j / NS) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 1); break; }
         uint8_t *xs = smem + L::kXs + s * L::kXsStride;
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
@@ -618,7 +647,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         if (!ok) set_abort(bars, err0, 3);
       }
       int band_r = -1, builds = 0;
-      for (int j = 0; ok && j < n_my; ++j) {
+      for (int j = 0; ok && j < n_all; ++j) {
         const int reg = j % kRegions, s = j % NS;
         const int r = tile_rule<BATCH>(p, first, j).r;
         if (r != band_r) {                 // the convert warps have built the bands for r
@@ -651,27 +680,70 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     // barrier wait holds up the other lanes of its warp.)
     if (lane == 0) {
       int issued = 0;
-      TileSeq<BATCH> lseq(p, first), sseq(p, first);
-      auto load_ctr = [&](int j) {
-        const int k = j % NR;
-        const Tile t = lseq.get(p);
-        if (j == 0 || BATCH) prefetch_tmap(t.ctr);
-        mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-        tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
-        lseq.next(p);
-        issued = j + 1;
-      };
-      for (int j = 0; j < n_my && j < NR; ++j) load_ctr(j);
-      for (int j = 0; j < n_my; ++j, sseq.next(p)) {
-        const int k = j % NR;
-        const Tile t = sseq.get(p);
-        if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
-        if (BATCH || !p.sums) {
-          tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
-          bulk_commit();
-          bulk_wait_read<0>();          // the store has read the entry
+      if constexpr (MS) {
+        int passed = 0;       // centre tiles loaded; steps whose loads may start
+        TileSeq<BATCH, true> lseq(p, first, n_my), sseq(p, first, n_my);
+        // loads the centre tiles up to (not including) tile `limit` whose step
+        // has passed its grid barrier, each into the entry its tile - NR freed
+        auto load_ctr = [&](int limit) {
+          while (issued < n_all && issued < limit && lseq.step <= passed) {
+            const int k = issued % NR;
+            const Tile t = lseq.get(p);
+            if (lseq.k == 0 || BATCH) prefetch_tmap(t.ctr);
+            mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
+            tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
+            lseq.next(p);
+            ++issued;
+          }
+        };
+        load_ctr(NR);
+        for (int j = 0; j < n_all; ++j, sseq.next(p)) {
+          const int k = j % NR;
+          const Tile t = sseq.get(p);
+          if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
+          if (BATCH || !p.sums) {
+            tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
+            bulk_commit();
+            bulk_wait_read<0>();          // the store has read the entry
+          }
+          if (!BATCH && sseq.k == n_my - 1 && sseq.step + 1 < n_steps) {
+            // this CTA's last tile of the step: its stores complete, then arrive
+            // and wait for every CTA before loading centre tiles of the next step
+            bulk_wait<0>();
+            fence_proxy_async_global();
+            gbar_arrive(p.gbar);
+            if (!gbar_wait(p.gbar, p.gbar_base + (uint32_t)(sseq.step + 1) * gridDim.x, &bars->abort, p.timeout_ns)) {
+              set_abort(bars, err0, 15);
+              break;
+            }
+            fence_proxy_async_global();
+            passed = sseq.step + 1;
+          }
+          load_ctr(j + 1 + NR);
         }
-        if (j + NR < n_my) load_ctr(j + NR);
+      } else {
+        TileSeq<BATCH> lseq(p, first), sseq(p, first);
+        auto load_ctr = [&](int j) {
+          const int k = j % NR;
+          const Tile t = lseq.get(p);
+          if (j == 0 || BATCH) prefetch_tmap(t.ctr);
+          mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
+          tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
+          lseq.next(p);
+          issued = j + 1;
+        };
+        for (int j = 0; j < n_my && j < NR; ++j) load_ctr(j);
+        for (int j = 0; j < n_my; ++j, sseq.next(p)) {
+          const int k = j % NR;
+          const Tile t = sseq.get(p);
+          if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
+          if (BATCH || !p.sums) {
+            tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
+            bulk_commit();
+            bulk_wait_read<0>();          // the store has read the entry
+          }
+          if (j + NR < n_my) load_ctr(j + NR);
+        }
       }
       bulk_wait<0>();                   // all writes complete before the CTA exits
       volatile int no_abort = 0;        // drain: the last load issued into each entry has landed
@@ -685,7 +757,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       const uint32_t idesc2 = idesc_f16acc(128, kTile);
       const uint32_t band16 = tmem + G::kBand16, band8 = tmem + G::kBand8P2;
       const OpDesc hop0 = op_descs(s_base + L::kH);
-      for (int j = 0; j < n_my; ++j) {
+      for (int j = 0; j < n_all; ++j) {
         if (!mbar_wait(&bars->h_full[j % NH], (j / NH) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, err0, 9); break; }
         tc_fence_after();
         const int reg = j % kRegions;
@@ -725,9 +797,18 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
-    if (ENC)
-      for (int j = 0; ok && j < n_my && j < L::NE; ++j) ok = encode(j, wtid, kCvtThreads);
-    for (int j = 0; ok && j < n_my; ++j) {
+    if (ENC && !MS)
+      for (int j = 0; ok && j < n_all && j < L::NE; ++j) ok = encode(j, wtid, kCvtThreads);
+    int enc_next = 0;   // MS: next window to encode
+    for (int j = 0; ok && j < n_all; ++j) {
+      if constexpr (ENC && MS) {
+        // windows up to j + NE - 1 (their buffers were read by passes 1 up to
+        // tile j - 1), but none of a later step than tile j: those wait on the
+        // grid barrier, which needs this CTA's remaining tiles of this step
+        const int lim = j + L::NE < n_all ? j + L::NE : n_all;
+        while (ok && enc_next < lim && enc_next / n_my <= j / n_my) ok = encode(enc_next++, wtid, kCvtThreads);
+        if (!ok) break;
+      }
       const int reg = j % kRegions;
       const int rj = tile_rule<BATCH>(p, first, j).r;
       const bool p2f16 = pass2_f16(DT, rj);
@@ -782,7 +863,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->h_full[j % NH]);
       // encode window j + NE into the buffer pass 1 of tile j has finished reading
-      if (ENC && j + L::NE < n_my && !(ok = encode(j + L::NE, wtid, kCvtThreads))) break;
+      if (ENC && !MS && j + L::NE < n_all && !(ok = encode(j + L::NE, wtid, kCvtThreads))) break;
     }
     if (!ok) set_abort(bars, err0, 8);
   } else {
@@ -801,8 +882,8 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     }
     bool ok = true;
     HalfRule hr = make_half_rule(BATCH ? RuleDev{} : p.rule, kScale);
-    TileSeq<BATCH> seq(p, first);
-    for (int j = 0; ok && j < n_my; ++j, seq.next(p)) {
+    TileSeq<BATCH, MS> seq(p, first, n_my);
+    for (int j = 0; ok && j < n_all; ++j, seq.next(p)) {
       const int reg = j % kRegions, k = j % NR;
       const Tile t = seq.get(p);
       const RuleDev &R = t.R;
@@ -894,13 +975,20 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
 
 template <int DT, bool ENC, bool BATCH, bool SW>
 __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_constant__ TcParams p) {
-  ltl_tc_body<DT, ENC, BATCH, SW, false>(p);
+  ltl_tc_body<DT, ENC, BATCH, SW, false, false>(p);
 }
 
 // One bit per cell: the same body under its own name, so that a profiler can
 // single it out.
 __global__ void __launch_bounds__(kThreads, 1) ltl_bits_kernel(const __grid_constant__ TcParams p) {
-  ltl_tc_body<1, true, false, false, true>(p);
+  ltl_tc_body<1, true, false, false, true, false>(p);
+}
+
+// Several steps of a single instance in one cooperative launch (separate
+// instantiations, so that the one-step kernels carry none of it).
+template <int DT, bool ENC, bool SW, bool BITS>
+__global__ void __launch_bounds__(kThreads, 1) ltl_tc_multi_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<DT, ENC, false, SW, BITS, true>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1220,6 +1308,19 @@ static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
+  }
+  if constexpr (!BATCH) {
+    if (p.n_steps > 1) {  // CTAs wait on one another: all must be resident at once
+      static bool configured_multi = false;
+      void (*multi)(TcParams) = tc::ltl_tc_multi_kernel<DT, ENC, SW, BITS>;
+      if (!configured_multi) {
+        cudaError_t e = cudaFuncSetAttribute(multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_multi = true;
+      }
+      void *args[] = {const_cast<TcParams *>(&p)};
+      return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(multi), dim3(grid), dim3(tc::kThreads), args, smem, s);
+    }
   }
   kern<<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();

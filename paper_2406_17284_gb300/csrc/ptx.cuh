@@ -91,6 +91,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Orders global-memory accesses of the generic proxy against those of the
+// async proxy (TMA) of the executing thread.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// ------------------------------------------------------- grid-wide barrier
+// A monotonic arrival counter in global memory shared by the CTAs of one
+// cooperative launch (all resident at once).  Arrive: one release add.
+__device__ __forceinline__ void gbar_arrive(uint32_t *ctr) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+}
+// Bounded wait until the counter has reached `target` (modulo 2^32); gives up
+// after `timeout_ns` or when *abort becomes non-zero.  Acquire semantics.
+__device__ __forceinline__ bool gbar_wait(const uint32_t *ctr, uint32_t target, volatile int *abort,
+                                          uint64_t timeout_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if ((int32_t)(v - target) >= 0) return true;
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > timeout_ns) return false;
+    __nanosleep(256);
+  }
+}
 
 // ------------------------------------------------------------------------ TMA
 __device__ __forceinline__ void prefetch_tmap(const void *tmap) {
