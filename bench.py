@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-bits", action="store_true", help="skip the one-bit-storage measurement")
     ap.add_argument("--no-vn", action="store_true", help="skip the simplified von Neumann measurement")
     ap.add_argument("--no-multistep", action="store_true", help="skip the several-steps-per-launch measurement")
+    ap.add_argument("--no-wide", action="store_true", help="skip the r > 16 measurement")
     return ap.parse_args()
 
 
@@ -383,6 +384,22 @@ def measure_multistep(torch, cat, inputs, stream, steps=64):
     return out
 
 
+def measure_wide(args, torch, cat, inputs, stream, d_init):
+    """Radii beyond 16 on the headline's grid: the FP16 fragment kernel with a second
+    halo fragment (five band fragments per reduction, FP32 step-2 accumulation)."""
+    n = args.size
+    out = {"workload": f"{n}x{n} bernoulli0.5, scaled rule C2 M1, FP16 fragment kernel (r > 16)"}
+    for r in (17, 24, 32):
+        g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="mma_sync", dtype="fp16")
+        g.set_state(d_init)
+        g.step(1, stream)
+        t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
+        assert g.status() == cat.CAT_OK
+        out[f"r{r}_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
+        g.close()
+    return out
+
+
 def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
     """One-bit storage: the headline's 16384^2 grid and 16 scaled rules stored 8 cells
     per byte (FP8 operands), stepped round-robin over the radii like the headline, so
@@ -546,6 +563,9 @@ def run_cat(args, rank, world, local):
     multistep = None
     if not args.no_multistep and rank == 0:
         multistep = measure_multistep(torch, cat, inputs, stream)
+    wide = None
+    if not args.no_wide and rank == 0:
+        wide = measure_wide(args, torch, cat, inputs, stream, d_init)
 
     cpu = None
     if rank == 0:
@@ -579,6 +599,7 @@ def run_cat(args, rank, world, local):
             "bits": bits,
             "von_neumann": vn,
             "multistep": multistep,
+            "wide_radius": wide,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII)},
             "cpu_baseline": cpu,

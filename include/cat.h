@@ -52,7 +52,11 @@ extern "C" {
 #define CAT_ERR_STATE (-6)       /* call out of order (e.g. stepping before a state) */
 
 /* LTL rule in the R C M S B N notation of Sec. V-A (Table IV lists instances).
- *   r      neighbourhood radius, 1 <= r <= 16 (the fragment-size limit of Sec. IV-A)
+ *   r      neighbourhood radius, 1 <= r <= 32.  Up to 16 (the fragment size,
+ *          Sec. IV-A) every kernel serves it; 17..32 (the extension with a
+ *          second halo fragment that Sec. VII describes) is served by the FP16
+ *          fragment kernel (MMA_SYNC, Moore) and the stencil, with uint8
+ *          storage and the zero boundary; CAT_KERNEL_AUTO picks them.
  *   C      number of states, 2 <= C <= 255
  *   M      1: the centre cell counts towards k; 0: it does not
  *   s1,s2  survival range for state-1 cells (inclusive; s1 > s2 means empty)

@@ -104,7 +104,7 @@ namespace {
 
 int validate_rule(const cat_rule_t *r) {
   if (!r) return fail(CAT_ERR_INVALID_ARG, "rule is NULL");
-  if (r->r < 1 || r->r > 16) return fail(CAT_ERR_INVALID_ARG, "radius %d outside [1, 16]", r->r);
+  if (r->r < 1 || r->r > 32) return fail(CAT_ERR_INVALID_ARG, "radius %d outside [1, 32]", r->r);
   if (r->C < 2 || r->C > 255) return fail(CAT_ERR_INVALID_ARG, "C = %d outside [2, 255]", r->C);
   if (r->M != 0 && r->M != 1) return fail(CAT_ERR_INVALID_ARG, "M must be 0 or 1");
   if (r->s1 < 0 || r->s2 < 0 || r->b1 < 0 || r->b2 < 0)
@@ -473,6 +473,8 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
     return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
   if (storage == CAT_STORE_BIT1 && rule->nbhd != 'M')
     return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served for the Moore neighbourhood only");
+  if (rule->r > 16 && (storage == CAT_STORE_BIT1 || boundary != CAT_BOUNDARY_ZERO))
+    return fail(CAT_ERR_UNSUPPORTED, "radii above 16 are served with uint8 storage and the zero boundary");
   cat_instance *h = new (std::nothrow) cat_instance();
   if (!h) return fail(CAT_ERR_OOM, "host allocation failed");
   if ((rc = device_info(&h->dev))) { delete h; return rc; }
@@ -484,9 +486,12 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   h->pitch = storage == CAT_STORE_BIT1 ? round_up((W + 7) / 8, 16) : round_up(W + 2 * h->ghost, 16);
   h->rule = *rule;
   h->rd = reduce_rule(*rule);
-  if (rule->nbhd == 'N' && rule->C > 2) {  // the cross with C > 2 runs on the CUDA-core stencil
+  if (rule->nbhd == 'N' && (rule->C > 2 || rule->r > 16)) {  // the cross with C > 2 or r > 16: CUDA-core stencil
     h->kernel = CAT_KERNEL_STENCIL;
     h->dtype = CAT_DTYPE_INT8;
+  } else if (rule->r > 16) {  // beyond the tcgen05 window: the paper's fragment scheme with two halo fragments
+    h->kernel = CAT_KERNEL_MMA_SYNC;
+    h->dtype = CAT_DTYPE_FP16;
   }
   const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
   cudaError_t e = cudaMalloc(&h->buf[0], bytes);
@@ -514,7 +519,9 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
   const bool vn = h->rule.nbhd == 'N';
-  if (kernel == CAT_KERNEL_AUTO) kernel = vn && h->rule.C > 2 ? CAT_KERNEL_STENCIL : CAT_KERNEL_TCGEN05;
+  const bool wide = h->rule.r > 16;
+  if (kernel == CAT_KERNEL_AUTO)
+    kernel = vn && (h->rule.C > 2 || wide) ? CAT_KERNEL_STENCIL : wide ? CAT_KERNEL_MMA_SYNC : CAT_KERNEL_TCGEN05;
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
   if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
     return fail(CAT_ERR_UNSUPPORTED, dtype == CAT_DTYPE_INT8 ? "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC"
@@ -522,6 +529,8 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves FP16 and INT8 operands");
   if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
+  if (wide && (kernel == CAT_KERNEL_TCGEN05 || (kernel == CAT_KERNEL_MMA_SYNC && (dtype != CAT_DTYPE_FP16 || vn))))
+    return fail(CAT_ERR_UNSUPPORTED, "radii above 16 are served by the FP16 fragment kernel (Moore) and the stencil");
   if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
     return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
   if (vn) {
@@ -607,7 +616,7 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   bool all_tc = true;   // Moore, zero boundary, uint8 storage: other instances step one by one
   for (int32_t i = 0; i < count; ++i) {
     all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8 &&
-              hs[i]->rule.nbhd == 'M';
+              hs[i]->rule.nbhd == 'M' && hs[i]->rule.r <= 16;
     if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
       return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
     if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)

@@ -238,13 +238,110 @@ __global__ void __launch_bounds__(kThreads) cat_mma_i8_kernel(const SimpleParams
   }
 }
 
+// ------------------------------------------------------- 16 < r <= 32, FP16
+// The extension the paper describes beyond the fragment size (Sec. VII): the
+// neighbours of a fragment reach two fragments away, so each reduction takes
+// five band fragments (offsets -2 .. 2) and the window carries a halo of two
+// fragments.  H <= 65 stays exact in FP16; the counts reach 65^2 = 4225 >
+// 2^11, so step 2 accumulates in FP32 (the paper's remark that FP16 stops
+// being precise enough at such radii).
+constexpr int kWideHF = 2;                          // halo fragments per side
+constexpr int WWX = TW + 32 * kWideHF, WHX = TH + 32 * kWideHF;
+constexpr size_t kWideSmem = (size_t)WHX * WWX * 2 + (size_t)WHX * TW * 2 + (size_t)TH * TW * 4 +
+                             2 * 5 * 256 * 2 + (size_t)TH * TW;
+
+__global__ void __launch_bounds__(kThreads) cat_wmma_f16_wide_kernel(const SimpleParams p) {
+  extern __shared__ __align__(128) uint8_t wide_smem[];
+  half *lam = reinterpret_cast<half *>(wide_smem);                 // WHX x WWX
+  half *qh = lam + WHX * WWX;                                       // WHX x TW  (H, all window rows)
+  float *qr = reinterpret_cast<float *>(qh + WHX * TW);             // TH x TW   (counts)
+  half *pk = reinterpret_cast<half *>(qr + TH * TW);                // step 1: P_d[k][n] = [|16d + k - n| <= r]
+  half *pm = pk + 5 * 256;                                          // step 2: A_d[m][k] = [|16d + k - m| <= r]
+  uint8_t *cst = reinterpret_cast<uint8_t *>(pm + 5 * 256);         // TH x TW centre states
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const RuleDev R = p.rule;
+  constexpr int H0 = 16 * kWideHF;                                  // halo width in cells
+
+  for (int i = tid; i < WHX * WWX; i += kThreads) {
+    const int y = i / WWX, x = i - y * WWX;
+    const int gy = y0 - H0 + y, gx = x0 - H0 + x;
+    uint8_t s = 0;
+    if (gy >= 0 && gy < p.H && gx >= 0 && gx < p.W) s = p.in[(int64_t)gy * p.pitch + gx];
+    lam[i] = __float2half(s == 1 ? 1.0f : 0.0f);
+    if (y >= H0 && y < H0 + TH && x >= H0 && x < H0 + TW) cst[(y - H0) * TW + (x - H0)] = s;
+  }
+  for (int i = tid; i < 5 * 256; i += kThreads) {
+    const int d = i / 256 - kWideHF, a = (i >> 4) & 15, b = i & 15;
+    const int e1 = 16 * d + a - b, e2 = 16 * d + b - a;
+    pk[i] = __float2half(e1 >= -R.r && e1 <= R.r ? 1.0f : 0.0f);   // a = k, b = n
+    pm[i] = __float2half(e2 >= -R.r && e2 <= R.r ? 1.0f : 0.0f);   // a = m, b = k
+  }
+  __syncthreads();
+
+  // Step 1: F^H_{i,j} = sum_d F_{i, j+d} P_d, every fragment row of the window.
+  for (int k = warp; k < (FH + 2 * kWideHF) * FW; k += kThreads / 32) {
+    const int i = k / FW, j = k - i * FW;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, half> F;
+    wmma::fill_fragment(F, __float2half(0.0f));
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, half, wmma::row_major> A;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, half, wmma::row_major> B;
+#pragma unroll
+    for (int d = -kWideHF; d <= kWideHF; ++d) {
+      wmma::load_matrix_sync(A, lam + (16 * i) * WWX + 16 * (j + kWideHF + d), WWX);
+      wmma::load_matrix_sync(B, pk + (d + kWideHF) * 256, 16);
+      wmma::mma_sync(F, A, B, F);
+    }
+    wmma::store_matrix_sync(qh + (16 * i) * TW + 16 * j, F, TW, wmma::mem_row_major);
+  }
+  __syncthreads();
+
+  // Step 2: F^R_{i,j} = sum_d A_d F^H_{i+d, j}, FP32 accumulation.
+  for (int k = warp; k < FH * FW; k += kThreads / 32) {
+    const int i = k / FW, j = k - i * FW;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> F;
+    wmma::fill_fragment(F, 0.0f);
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, half, wmma::row_major> A;
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, half, wmma::row_major> B;
+#pragma unroll
+    for (int d = -kWideHF; d <= kWideHF; ++d) {
+      wmma::load_matrix_sync(A, pm + (d + kWideHF) * 256, 16);
+      wmma::load_matrix_sync(B, qh + (16 * (i + kWideHF + d)) * TW + 16 * j, TW);
+      wmma::mma_sync(F, A, B, F);
+    }
+    wmma::store_matrix_sync(qr + (16 * i) * TW + 16 * j, F, TW, wmma::mem_row_major);
+  }
+  __syncthreads();
+
+  for (int i = tid; i < TH * TW; i += kThreads) {
+    const int y = i / TW, x = i - y * TW;
+    const int gy = y0 + y, gx = x0 + x;
+    if (gy >= p.H || gx >= p.W) continue;
+    const int s = __float2int_rn(qr[i]);
+    if (p.sums) p.sums[(int64_t)gy * p.sums_ld + gx] = s;
+    else p.out[(int64_t)gy * p.pitch + gx] = (uint8_t)next_state(s, cst[i], R);
+  }
+}
+
 }  // namespace frag
 
-// dt follows cat.h: 1 = FP16, 3 = INT8.
+// dt follows cat.h: 1 = FP16, 3 = INT8.  FP16 with r > 16 runs the wide kernel.
 cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s) {
   dim3 grid((p.W + frag::TW - 1) / frag::TW, (p.H + frag::TH - 1) / frag::TH);
-  if (dt == 3) frag::cat_mma_i8_kernel<<<grid, frag::kThreads, 0, s>>>(p);
-  else frag::cat_wmma_f16_kernel<<<grid, frag::kThreads, 0, s>>>(p);
+  if (dt == 3) {
+    frag::cat_mma_i8_kernel<<<grid, frag::kThreads, 0, s>>>(p);
+  } else if (p.rule.r > 16) {
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(frag::cat_wmma_f16_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)frag::kWideSmem);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    frag::cat_wmma_f16_wide_kernel<<<grid, frag::kThreads, frag::kWideSmem, s>>>(p);
+  } else {
+    frag::cat_wmma_f16_kernel<<<grid, frag::kThreads, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
     int rc = cat::host_validate_rule(&g.rule);
     if (rc) return rc;
     if (g.rule.nbhd != 'M') return err(CAT_ERR_UNSUPPORTED, "grid %lld: the static batch serves the Moore neighbourhood", i);
+    if (g.rule.r > 16) return err(CAT_ERR_UNSUPPORTED, "grid %lld: the static batch serves radii up to 16", i);
     encode |= g.rule.C > 2;
     n_tiles += ((g.H + 127) / 128) * ((g.W + 127) / 128);
   }

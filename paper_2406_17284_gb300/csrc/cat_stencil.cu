@@ -11,7 +11,7 @@ namespace stencil {
 
 constexpr int BX = 32, BY = 32;           // output tile
 constexpr int kThreads = 256;             // 32 x 8 threads, 4 rows each
-constexpr int kMaxR = 16;
+constexpr int kMaxR = 32;
 constexpr int SW = BX + 2 * kMaxR, SH = BY + 2 * kMaxR;
 
 __device__ __forceinline__ uint32_t next_state(int s, uint32_t c, const RuleDev &R) {

@@ -128,7 +128,7 @@ def pin_band_product(lib):
     """Oracle box sums == the paper's two band products, both boundaries."""
     rng = np.random.default_rng(11)
     for (H, W) in [(1, 1), (3, 5), (7, 4), (12, 12), (17, 9), (20, 33)]:
-        for r in (0, 1, 2, 3, 5, 8, 16):
+        for r in (0, 1, 2, 3, 5, 8, 16, 24, 32):
             for C in (2, 4):
                 g = rng.integers(0, C, size=(H, W), dtype=np.uint8)
                 for periodic in (False, True):
@@ -149,7 +149,7 @@ def pin_all_ones(lib):
     """All-ones grid, zero halo: S(y,x) = clipped box area (max (2r+1)^2 = 1089)."""
     for (H, W) in [(40, 40), (70, 45), (3, 100)]:
         g = np.ones((H, W), np.uint8)
-        for r in (1, 2, 9, 16):
+        for r in (1, 2, 9, 16, 32):
             y = np.arange(H)[:, None]
             x = np.arange(W)[None, :]
             area = (np.minimum(y + r, H - 1) - np.maximum(y - r, 0) + 1) * \
@@ -157,11 +157,12 @@ def pin_all_ones(lib):
             assert np.array_equal(oracle.box_sums(g, r, lib=lib), area), (H, W, r)
     g = np.ones((80, 80), np.uint8)
     assert oracle.box_sums(g, 16, lib=lib)[40, 40] == 33 * 33
+    assert oracle.box_sums(g, 32, lib=lib)[40, 40] == 65 * 65
 
 
 def pin_impulse(lib):
     """A single live cell gives S = the (2r+1)^2 box of ones around it (band impulse response)."""
-    for r in (1, 3, 8, 16):
+    for r in (1, 3, 8, 16, 25):
         n = 2 * r + 9
         g = np.zeros((n, n + 3), np.uint8)
         cy, cx = n // 2, n // 2 + 1

@@ -46,7 +46,8 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
         (0, 10, good, 0, cat.CAT_ERR_INVALID_ARG),
         (10, 0, good, 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(0, 2, 0, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
-        (10, 10, cat.make_rule(17, 2, 0, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
+        (10, 10, cat.make_rule(33, 2, 0, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
+        (10, 10, cat.make_rule(17, 2, 0, 2, 3, 3, 3), 1, cat.CAT_ERR_UNSUPPORTED),   # r > 16: zero boundary only
         (10, 10, cat.make_rule(1, 1, 0, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 2, 2, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),
         (10, 10, cat.make_rule(1, 2, 0, -1, 3, 3, 3), 0, cat.CAT_ERR_INVALID_ARG),

@@ -1,0 +1,143 @@
+"""Radii 17..32 vs the CPU oracle, cell by cell.
+
+Beyond the fragment size the paper extends its scheme with a second halo
+fragment and five band fragments per reduction (Sec. VII); the FP16 fragment
+kernel does that, with FP32 accumulation in step 2 since the counts reach
+65^2 = 4225.  The CUDA-core stencil serves these radii too (and the simplified
+von Neumann cross).  The tcgen05 kernels stop at r = 16 and refuse larger
+radii; CAT_KERNEL_AUTO picks the fragment kernel.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2406_17284_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = [("mma_sync", "fp16"), ("stencil", "auto"), ("auto", "auto")]
+KIDS = ["mma_sync-fp16", "stencil", "auto"]
+RADII = (17, 20, 24, 31, 32)
+
+
+@pytest.fixture(scope="module")
+def cat():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2406_17284_gb300 import build
+    build.build()
+    from paper_2406_17284_gb300 import cat as catmod
+    catmod.load()
+    return catmod
+
+
+def orule(d):
+    return oracle.Rule(d["r"], d["C"], d["M"], d["s1"], d["s2"], d["b1"], d["b2"], d.get("nbhd", "M"))
+
+
+def assert_same(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        y, x = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} cells differ, first at ({y},{x}): got {got[y, x]} want {want[y, x]}")
+
+
+def run(cat, kernel, dtype, grid, rule, steps):
+    g = cat.Grid(grid.shape[0], grid.shape[1], rule, kernel=kernel, dtype=dtype)
+    try:
+        g.set_state(grid)
+        g.step(steps)
+        out = g.get_state()
+        assert g.status() == cat.CAT_OK
+        return out
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("kernel,dtype", KERNELS, ids=KIDS)
+def test_counts(cat, kernel, dtype):
+    grid = inputs.bernoulli(300, 437, 0.5, 17)
+    ones = np.ones((200, 230), np.uint8)
+    for r in RADII:
+        for g_ in (grid, ones):
+            g = cat.Grid(*g_.shape, inputs.scaled_rule(r), kernel=kernel, dtype=dtype)
+            try:
+                g.set_state(g_)
+                assert_same(g.box_sums(), oracle.box_sums(g_, r), f"S r={r}")
+            finally:
+                g.close()
+    assert oracle.box_sums(ones, 32)[100, 100] == 65 * 65
+
+
+@pytest.mark.parametrize("kernel,dtype", KERNELS, ids=KIDS)
+def test_steps(cat, kernel, dtype):
+    """The radius-scaled rule, M0 and M1, 3 steps on ragged shapes."""
+    for i, (H, W) in enumerate([(384, 523), (130, 70), (1, 300), (257, 1)]):
+        for r in RADII:
+            rule = inputs.scaled_rule(r, M=(r + i) % 2)
+            grid = inputs.bernoulli(H, W, 0.5, 1000 + 37 * i + r)
+            want = oracle.step(grid, orule(rule), n_steps=3)
+            assert_same(run(cat, kernel, dtype, grid, rule, 3), want, f"{H}x{W} r={r}")
+
+
+def test_multistate_and_cross(cat):
+    """C > 2 on the fragment kernel and the stencil; the simplified von Neumann
+    cross with r > 16 on the stencil (AUTO picks it)."""
+    rule = dict(r=20, C=6, M=1, s1=300, s2=900, b1=350, b2=700)
+    grid = inputs.uniform_states(260, 300, 6, 77)
+    want = oracle.step(grid, orule(rule), n_steps=4)
+    assert_same(run(cat, "mma_sync", "fp16", grid, rule, 4), want, "C=6 fragment")
+    assert_same(run(cat, "stencil", "auto", grid, rule, 4), want, "C=6 stencil")
+    cross = inputs.vn_scaled_rule(28)
+    g2 = inputs.bernoulli(300, 280, 0.5, 78)
+    want = oracle.step(g2, orule(cross), n_steps=3)
+    assert_same(run(cat, "auto", "auto", g2, cross, 3), want, "cross r=28")
+
+
+def test_unsupported(cat):
+    rule = inputs.scaled_rule(20)
+    for kernel, dtype in (("tcgen05", "fp8"), ("tcgen05", "fp16"), ("mma_sync", "int8")):
+        with pytest.raises(cat.CatError) as e:
+            cat.Grid(64, 64, rule, kernel=kernel, dtype=dtype)
+        assert e.value.code == cat.CAT_ERR_UNSUPPORTED, (kernel, dtype)
+    with pytest.raises(cat.CatError) as e:
+        cat.Grid(64, 64, inputs.vn_scaled_rule(20), kernel="mma_sync", dtype="fp16")
+    assert e.value.code == cat.CAT_ERR_UNSUPPORTED
+    for kw in (dict(boundary=cat.BOUNDARY_PERIODIC), dict(storage=cat.STORE_BIT1)):
+        with pytest.raises(cat.CatError) as e:
+            cat.Grid(64, 64, rule, **kw)
+        assert e.value.code == cat.CAT_ERR_UNSUPPORTED, kw
+
+
+def test_full_4096_sampled_windows(cat):
+    """4096^2 Bernoulli(0.5), r = 24 and 32, two steps of the fragment kernel
+    checked on 12 windows (corners included) and equal to the stencil everywhere."""
+    import torch
+    N = 4096
+    host = inputs.bernoulli(N, N, 0.5, 4242)
+    d = torch.from_numpy(host).cuda()
+    rng = np.random.default_rng(3)
+    for r in (24, 32):
+        rule = inputs.scaled_rule(r)
+        a = cat.Grid(N, N, rule, kernel="mma_sync", dtype="fp16")
+        b = cat.Grid(N, N, rule, kernel="stencil", dtype="auto")
+        try:
+            a.set_state(d)
+            b.set_state(d)
+            a.step(2)
+            b.step(2)
+            torch.cuda.synchronize()
+            assert a.status() == cat.CAT_OK and b.status() == cat.CAT_OK
+            out = a.state_tensor()
+            assert int((out != b.state_tensor()).sum()) == 0, f"r={r}: fragment kernel and stencil differ"
+            spots = [(0, 0), (0, N - 200), (N - 200, 0), (N - 200, N - 200)] + \
+                [tuple(int(v) for v in rng.integers(0, N - 200, 2)) for _ in range(8)]
+            for (y0, x0) in spots:
+                ya, xa = max(0, y0 - 2 * r), max(0, x0 - 2 * r)
+                yb, xb = min(N, y0 + 200 + 2 * r), min(N, x0 + 200 + 2 * r)
+                want = oracle.step(host[ya:yb, xa:xb], orule(rule), n_steps=2)[y0 - ya:y0 - ya + 200, x0 - xa:x0 - xa + 200]
+                assert_same(out[y0:y0 + 200, x0:x0 + 200].cpu().numpy(), want, f"r={r} window ({y0},{x0})")
+        finally:
+            a.close()
+            b.close()
