@@ -181,6 +181,19 @@ CAT_API int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t d
  * up to 16 bytes).                                                          */
 CAT_API int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch);
 
+/* Makes the instance step two caller-owned device buffers instead of its own
+ * (for a framework whose allocator owns the memory, e.g. two torch tensors):
+ * a and b hold H rows of W cells at `pitch` bytes (pitch >= W and a multiple
+ * of 16; both 16-byte aligned, device memory, distinct).  The current state
+ * is taken from a as it is (no copy); after a step the state is in b, then a
+ * again, as cat_state_ptr reports.  The instance's own buffers are freed; the
+ * library never frees bound ones (cat_destroy leaves them to the caller, who
+ * must keep them alive while the instance uses them).  Synchronises the
+ * device.  Zero boundary and uint8 storage only (UNSUPPORTED otherwise, and
+ * for a later change to one-bit storage).  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA.                                                                     */
+CAT_API int cat_bind(cat_handle_t h, uint8_t *a, uint8_t *b, int64_t pitch);
+
 /* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`
  * (one kernel launch per step; the buffers swap after every step).          */
 CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);

@@ -34,7 +34,7 @@ DTYPES = {"auto": DTYPE_AUTO, "fp16": DTYPE_FP16, "fp8": DTYPE_FP8_E4M3, "int8":
 KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MMA_SYNC,
            "stencil": KERNEL_STENCIL}
 
-EXPORTED = ["cat_create", "cat_create_ex", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
+EXPORTED = ["cat_create", "cat_create_ex", "cat_bind", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
             "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
             "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static"]
 
@@ -87,6 +87,7 @@ def load(path: str | None = None):
             "cat_set_state": [h, p, i64, i32, p],
             "cat_get_state": [h, p, i64, i32, p],
             "cat_state_ptr": [h, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)],
+            "cat_bind": [h, p, p, i64],
             "cat_step": [h, i64, p],
             "cat_batch_step": [ctypes.POINTER(ctypes.c_void_p), i32, i64, p],
             "cat_box_sums": [h, p, i64, p],
@@ -156,6 +157,10 @@ def cat_state_ptr(h: int) -> tuple[int, int]:
     p, pitch = ctypes.c_void_p(), ctypes.c_int64()
     _check(load().cat_state_ptr(h, ctypes.byref(p), ctypes.byref(pitch)))
     return p.value, pitch.value
+
+
+def cat_bind(h: int, a_ptr: int, b_ptr: int, pitch: int):
+    _check(load().cat_bind(h, a_ptr, b_ptr, pitch))
 
 
 def cat_step(h: int, n_steps: int = 1, stream=None):

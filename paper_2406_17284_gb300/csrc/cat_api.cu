@@ -95,6 +95,7 @@ struct cat_instance {
   int32_t inject = 0;
   uint64_t timeout_ns = 2000000000ull;
   int32_t steps_per_launch = 1;  // > 1: cooperative launches of several steps
+  bool owns_buffers = true;      // false after cat_bind: the caller owns buf[0], buf[1]
   uint32_t gbar_count = 0;       // arrivals on the grid-barrier counter (d_err[1]) so far
   // grid cell (0, 0) of buffer b (past the ghost frame when there is one)
   uint8_t *origin(int b) const { return buf[b] + ghost * pitch + ghost; }
@@ -549,6 +550,8 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   }
   if (steps_per_launch > 1 && (kernel != CAT_KERNEL_TCGEN05 || vn || h->ghost))
     return fail(CAT_ERR_UNSUPPORTED, "several steps per launch are served by the tcgen05 Moore kernel with the zero boundary");
+  if (storage != h->storage && !h->owns_buffers)
+    return fail(CAT_ERR_UNSUPPORTED, "an instance on bound buffers keeps uint8 storage");
   if (storage != h->storage) {
     int rc = change_storage(h, storage);
     if (rc) return rc;
@@ -706,12 +709,40 @@ int cat_debug_control(cat_handle_t h, int32_t what, int64_t value) {
   }
 }
 
+int cat_bind(cat_handle_t h, uint8_t *a, uint8_t *b, int64_t pitch) {
+  if (!h || !a || !b || a == b) return fail(CAT_ERR_INVALID_ARG, "NULL handle or buffers, or a == b");
+  if (pitch < h->W || pitch % 16 != 0) return fail(CAT_ERR_INVALID_ARG, "pitch must be >= W and a multiple of 16");
+  if (((uintptr_t)a | (uintptr_t)b) % 16 != 0) return fail(CAT_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  if (h->ghost || h->storage != CAT_STORE_U8)
+    return fail(CAT_ERR_UNSUPPORTED, "bound buffers are served with the zero boundary and uint8 storage");
+  cudaPointerAttributes at{}, bt{};
+  if (cudaPointerGetAttributes(&at, a) != cudaSuccess || cudaPointerGetAttributes(&bt, b) != cudaSuccess ||
+      at.type != cudaMemoryTypeDevice || bt.type != cudaMemoryTypeDevice) {
+    (void)cudaGetLastError();
+    return fail(CAT_ERR_INVALID_ARG, "buffers must be device memory");
+  }
+  CAT_CUDA(cudaDeviceSynchronize());
+  drop_plans_with(h);
+  if (h->owns_buffers) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+  }
+  h->buf[0] = a;
+  h->buf[1] = b;
+  h->pitch = pitch;
+  h->cur = 0;
+  h->owns_buffers = false;
+  return build_maps(h);
+}
+
 int cat_destroy(cat_handle_t h) {
   if (!h) return CAT_OK;
   cudaDeviceSynchronize();
   drop_plans_with(h);
-  cudaFree(h->buf[0]);
-  cudaFree(h->buf[1]);
+  if (h->owns_buffers) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+  }
   cudaFree(h->d_err);
   delete h;
   return CAT_OK;

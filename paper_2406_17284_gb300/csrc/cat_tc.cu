@@ -545,7 +545,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
 
   // ---- set-up: barriers, TMEM, bands ------------------------------------
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kMaxStages; ++i) {   // every stage and ring entry a layout can use
       mbar_init(&bars->x_full[i], 1);
       mbar_init(&bars->x_empty[i], ENC ? kCvtWarps : 1);  // encoders, or pass 1's commit
       mbar_init(&bars->c_full[i], 1);

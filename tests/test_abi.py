@@ -79,3 +79,4 @@ def test_null_handles_rejected(lib):
     assert lib.cat_status(None, None) == cat.CAT_ERR_INVALID_ARG
     assert lib.cat_destroy(None) == cat.CAT_OK
     assert lib.cat_batch_step(None, 1, 1, None) == cat.CAT_ERR_INVALID_ARG
+    assert lib.cat_bind(None, None, None, 16) == cat.CAT_ERR_INVALID_ARG
