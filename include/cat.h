@@ -200,9 +200,14 @@ CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);
 
 /* Advances `count` independent instances by n_steps each.  The instances may
  * differ in size, radius and rule but must share kernel and dtype options.
- * Each step is ONE persistent launch over a flat tile work-list of all
- * instances; when `stream` is not capturing, the n_steps launches are
- * replayed from a CUDA graph cached for this handle list.                   */
+ * When all of them run the tcgen05 kernel on the Moore neighbourhood with
+ * r <= 16, the zero boundary and uint8 storage, each step is ONE persistent
+ * launch over a flat tile work-list of all instances, and when `stream` is
+ * not capturing the n_steps launches are replayed from a CUDA graph cached
+ * for this handle list; otherwise every instance is stepped by its own
+ * launches, one step at a time.  Errors: INVALID_ARG (NULL or repeated
+ * handles, mixed options), UNSUPPORTED (a batched instance above 4194176
+ * cells per side), OOM, CUDA.                                              */
 CAT_API int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream);
 
 /* Debug/verification: writes the counts of the current state, computed by
