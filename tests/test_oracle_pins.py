@@ -42,6 +42,19 @@ def test_scaled_rule_half_up_rounding():
     assert inputs.scaled_rule_ranges(7) == (77, 131, 77, 101)
     assert inputs.scaled_rule_ranges(12) == (213, 363, 213, 281)
     assert inputs.scaled_rule_ranges(1) == (3, 5, 3, 4)
+    # r = 32 (n = 4225): 0.34n and 0.58n are ties again
+    assert inputs.scaled_rule_ranges(32) == (1437, 2451, 1437, 1901)
+
+
+def test_cross_scaled_rule_ranges():
+    """The cross rule scales with n = 4r + 1 (the centre once): r = 1 -> n = 5,
+    r = 5 -> n = 21, r = 16 -> n = 65, r = 32 -> n = 129."""
+    from paper_2406_17284_gb300 import inputs
+    assert inputs.vn_scaled_rule_ranges(1) == (2, 3, 2, 2)
+    assert inputs.vn_scaled_rule_ranges(5) == (7, 12, 7, 9)
+    assert inputs.vn_scaled_rule_ranges(16) == (22, 38, 22, 29)
+    assert inputs.vn_scaled_rule_ranges(32) == (44, 75, 44, 58)
+    assert inputs.vn_scaled_rule(3)["nbhd"] == "N"
 
 
 def test_oracle_rejects_bad_input():
