@@ -163,6 +163,83 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# Algorithmic tensor work per cell update: the paper's own granularity, six
+# 16x16x16 MMAs per 16x16 fragment of cells (Sec. IV, Alg. 1), 192 flops per
+# cell for every r <= 16.  What a kernel executes beyond that is overhead.
+FLOPS_PER_CELL = 192.0
+
+
+def measure_tensor_peaks(torch, cat, stream):
+    """Dense tcgen05 MMA rates of this GPU (cat_tensor_probe: one CTA per SM issuing
+    M=128 N=256 MMAs back to back): burst = median of ten ~2 ms launches,
+    sustained = one launch of ~1 s.  TFLOP/s per operand dtype."""
+    sms = torch.cuda.get_device_properties(stream.device).multi_processor_count
+    status = torch.zeros(1, dtype=torch.int32, device=stream.device)
+    out = {}
+    for name, dt, K in (("e4m3", cat.DTYPE_FP8_E4M3, 32), ("f16", cat.DTYPE_FP16, 16)):
+        def flops(n):
+            return sms * n * 2.0 * 128 * 256 * K
+        n_burst, n_sus = 1 << 15, 1 << 23
+        for _ in range(3):
+            cat.cat_tensor_probe(dt, n_burst, status.data_ptr(), stream)
+        t = time_launches(torch, lambda: cat.cat_tensor_probe(dt, n_burst, status.data_ptr(), stream), 10, stream)
+        burst = flops(n_burst) / (statistics.median(t) / 1000.0) / 1e12
+        t = time_launches(torch, lambda: cat.cat_tensor_probe(dt, n_sus, status.data_ptr(), stream), 1, stream)
+        sustained = flops(n_sus) / (t[0] / 1000.0) / 1e12
+        torch.cuda.synchronize()
+        if int(status.item()) != 0:
+            raise RuntimeError(f"tensor probe ({name}) timed out")
+        out[name] = {"burst_tflops": burst, "sustained_tflops": sustained}
+    out["how"] = ("cat_tensor_probe: one CTA per SM, one thread issuing tcgen05.mma M=128 N=256 (K=32 e4m3 "
+                  "kind::f8f6f4 / K=16 f16 kind::f16), f32 accumulators; burst = median of 10 launches of "
+                  "2^15 MMAs per SM, sustained = one launch of 2^23")
+    return out
+
+
+def roof(value, bytes_per_cell, tensor_tflops, hbm_gbs, tensor_src="e4m3 burst"):
+    """The roofline of a path in cell-updates/s: the slower of the HBM term (state
+    bytes per cell update at the measured copy rate) and the tensor term (192
+    flops per cell update at the operand dtype's measured dense rate; None where
+    the path does not run on tcgen05), and value's fraction of it."""
+    hbm_term = hbm_gbs * 1e9 / bytes_per_cell
+    tensor_term = tensor_tflops * 1e12 / FLOPS_PER_CELL if tensor_tflops else None
+    bound = "tensor" if tensor_term is not None and tensor_term < hbm_term else "hbm"
+    rl = min(hbm_term, tensor_term) if tensor_term is not None else hbm_term
+    return {"bound": bound, "roofline_cell_updates_per_s": rl, "frac": value / rl,
+            "hbm_term": hbm_term, "tensor_term": tensor_term, "bytes_per_cell": bytes_per_cell,
+            "tensor_peak": tensor_src if tensor_term is not None else None}
+
+
+def host_link(torch, dev, nbytes=256 << 20, reps=5):
+    """Plain pinned-memory copies of nbytes: host->device, device->host, and both at
+    once on two streams (GB/s, median of reps, CUDA events)."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    out = {}
+    for name, fn in (("h2d_gbs", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_gbs", lambda: h.copy_(d, non_blocking=True))):
+        with torch.cuda.stream(s1):
+            fn()
+            t = time_launches(torch, fn, reps, s1)
+        out[name] = nbytes / (statistics.median(t) / 1000.0) / 1e9
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    out["bidirectional_gbs_each_way"] = nbytes / statistics.median(ts) / 1e9
+    out["bytes"] = nbytes
+    return out
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_sample(rows: int, radii, steps: int = 1, width: int = N):
     """Times the oracle (as it stands) on the first `rows` full-width rows of the
@@ -193,7 +270,9 @@ def run_reference(args, rank, world):
         vals.append(v)
         t_all += dt
     value = statistics.median(vals)
-    ms_per_step = 1000.0 * (N * N * len(RADII)) / value
+    # measured wall time of one reference step: one step per radius of the
+    # sampled band (side rows x N columns), not a projection to the full grid
+    ms_per_step = 1000.0 * t_all / args.steps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -201,6 +280,8 @@ def run_reference(args, rank, world):
         "config": {"workload": f"radius_sweep_{N}x{N}_r1-16_bernoulli0.5", "grid": [N, N], "radii": RADII,
                    "rule": "R_r C2 M1 S0.34n..0.58n B0.34n..0.45n NM", "boundary": "zero",
                    "l2": "inputs larger than L2"},
+        "step": f"one step per r in {RADII[0]}..{RADII[-1]} of the first {side} rows x {N} columns "
+                f"({side * N * len(RADII)} cell updates, measured)",
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {side} rows x {N} columns of the 16384^2 grid, one step per r in {RADII[0]}..{RADII[-1]}"},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -436,6 +517,9 @@ def run_cat(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    tensor_peaks = measure_tensor_peaks(torch, cat, stream)
+    e4m3_peak = tensor_peaks["e4m3"]["burst_tflops"]
+    f16_peak = tensor_peaks["f16"]["burst_tflops"]
     host = inputs.bernoulli(n, n, P_ALIVE, SEED + rank)
     d_init = torch.from_numpy(host).to(dev)
     grids = {}
@@ -490,7 +574,20 @@ def run_cat(args, rank, world, local):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     alg_bytes = 2.0 * n * n  # read + write of one uint8 state per cell
-    achieved = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
+    achieved_all = alg_bytes / (avg_launch_ms / 1000.0) / 1e9
+    # the dominant kernel: with FP8 operands the short-window instantiation
+    # serves r <= 7 and the standard one r >= 8; the one with the larger share
+    # of the launch time is reported
+    kern_of = {r: ("ltl_tc_kernel<FP8, short window>" if args.dtype == "fp8" and r <= 7
+                   else f"ltl_tc_kernel<{args.dtype.upper()}, standard window>") for r in RADII}
+    share = {}
+    for r, ms in per_r.items():
+        share[kern_of[r]] = share.get(kern_of[r], 0.0) + ms
+    dom = max(share, key=share.get)
+    dom_ms = statistics.mean(ms for r, ms in per_r.items() if kern_of[r] == dom)
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    tpeak = e4m3_peak if args.dtype == "fp8" else f16_peak
+    dom_roof = roof(n * n / (dom_ms / 1000.0), 2.0, tpeak, hbm)
 
     # ---- e2e: same metric through the C ABI from pinned host memory.  Every
     # step of every grid copies its input in (cat_set_state), steps it and
@@ -527,6 +624,8 @@ def run_cat(args, rank, world, local):
     torch.cuda.synchronize()
     te = (time.perf_counter() - te0) / e2e_steps
     e2e_value = cells_per_step * world / te
+
+    link = host_link(torch, dev)
 
     # ---- comparators on the same inputs (median of a few launches per r)
     comps = {}
@@ -575,6 +674,28 @@ def run_cat(args, rank, world, local):
 
     for g in grids.values():
         g.close()
+
+    # every figure next to its own roofline (state bytes per cell update; the
+    # tensor term where the path runs on tcgen05, at that operand dtype's rate)
+    def roofs(d, keys, bpc, tflops):
+        if d is not None:
+            d["roofline"] = {k: roof(d[k], bpc, tflops, hbm) for k in keys if d.get(k)}
+    if batched:
+        roofs(batched, ["fp8_tcgen05_batched"], 2.0, e4m3_peak)
+        batched["roofline"].update({k: roof(batched[k], 2.0, f16_peak, hbm, "f16 burst")
+                                    for k in ["fp16_tcgen05_batched"] if batched.get(k)})
+        batched["roofline"].update({k: roof(batched[k], 2.0, None, hbm)
+                                    for k in ["fp16_paper_mma_sync_per_grid"] if batched.get(k)})
+    roofs(multistate, ["single_cell_updates_per_s", "batch_256x2048_cell_updates_per_s"], 2.0, e4m3_peak)
+    roofs(periodic, [k for k in (periodic or {}) if k.endswith("_per_s")], 2.0, e4m3_peak)
+    roofs(bits, ["cell_updates_per_s"], 0.25, e4m3_peak)
+    roofs(vn, ["cell_updates_per_s"], 2.0, e4m3_peak)
+    roofs(multistep, [k for k in (multistep or {}) if k.endswith("_per_s")], 2.0, e4m3_peak)
+    roofs(wide, [k for k in (wide or {}) if k.endswith("_per_s")], 2.0, None)
+    comp_roofs = {}
+    for k, row in comps.items():
+        tp = f16_peak if k == "tcgen05/fp16" else e4m3_peak if k == "tcgen05/fp8" else None
+        comp_roofs[k] = {str(r): roof(v, 2.0, tp, hbm)["frac"] for r, v in row.items()}
     if rank == 0:
         per_r_rate = {str(r): n * n / (ms / 1000.0) for r, ms in sorted(per_r.items())}
         line = {
@@ -588,11 +709,21 @@ def run_cat(args, rank, world, local):
                        "kernel": f"tcgen05/{args.dtype}", "l2": "inputs (256 MiB per grid) larger than L2",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": args.steps * len(RADII),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "roofline": {"bound": dom_roof["bound"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic(args.dtype, n * n),
-                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": f"ltl_tc_kernel ({args.dtype})"},
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "kernel": dom,
+                         "kernel_radii": [r for r in RADII if kern_of[r] == dom],
+                         "kernel_time_share": share[dom] / sum(share.values()),
+                         "hbm_term_cell_updates_per_s": dom_roof["hbm_term"],
+                         "tensor_term_cell_updates_per_s": dom_roof["tensor_term"],
+                         "tensor_term": f"{FLOPS_PER_CELL:.0f} flops per cell update at the measured "
+                                        f"{'e4m3' if args.dtype == 'fp8' else 'f16'} burst rate {tpeak:.0f} TFLOP/s",
+                         "all_radii": {"achieved": achieved_all, "frac": achieved_all / hbm}},
+            "tensor_peaks_tflops": tensor_peaks,
+            "roofline_whole_sweep": roof(value / world, 2.0, tpeak, hbm),
             "per_r_cell_updates_per_s": per_r_rate,
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
+            "comparators_roofline_frac": comp_roofs,
             "batched": batched,
             "multistate": multistate,
             "periodic": periodic,
@@ -601,7 +732,8 @@ def run_cat(args, rank, world, local):
             "multistep": multistep,
             "wide_radius": wide,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
-                    "d2h_bytes_per_step": n * n * len(RADII)},
+                    "d2h_bytes_per_step": n * n * len(RADII), "host_link": link,
+                    "link_bound_cell_updates_per_s": link["bidirectional_gbs_each_way"] * 1e9 * world},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
         }

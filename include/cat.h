@@ -79,9 +79,17 @@ typedef struct cat_rule {
 
 enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
 
-/* Operand precision of the two band products.  Counts are exact in all of
- * them: FP16 holds every integer <= 2048 (Sec. V-A), FP8 e4m3 holds 0..16 and
- * the pass-2 input is split into an exact low and high part when r >= 8.      */
+/* Operand precision of the two band products (Sec. V-A uses FP16; the others
+ * are the lower-precision types Sec. VI names).  Counts are exact in all of
+ * them, so every dtype gives the same next states:
+ *   FP16      holds every integer <= 2048: the cell states, the band and the
+ *             horizontal sums H <= 2r+1 are exact, and so is every partial sum.
+ *   FP8_E4M3  a state byte 0x01 read as e4m3 is 2^-9, so the raw bytes are the
+ *             pass-1 operand; H * 2^-9 is an e4m3 number while H <= 15
+ *             (2r+1 <= 15).  Beyond that the TCGEN05 kernel passes H to the
+ *             second product as f16 operands.
+ *   INT8      H <= 65 < 127; served by MMA_SYNC (sm_103a has no tcgen05 kind::i8).
+ *   FP4_E2M1  not served by this build (UNSUPPORTED).                         */
 enum {
   CAT_DTYPE_AUTO = 0,
   CAT_DTYPE_FP16 = 1,
@@ -129,8 +137,12 @@ typedef struct cat_instance *cat_handle_t;
  * 16), refreshed by a small kernel before every step, and is stepped by the
  * tcgen05 kernel only.  The state is all zero until cat_set_state.  The
  * instance owns its buffers; cat_destroy frees them.  Uses the current CUDA
- * device.  Errors: INVALID_ARG (H or W < 1, H*W > 2^40, bad rule, unknown
- * boundary), UNSUPPORTED (nbhd != 'M'), OOM, CUDA.                          */
+ * device.  The kernel defaults to TCGEN05 with FP8 operands; r > 16 selects
+ * MMA_SYNC with FP16 operands, and the simplified von Neumann cross with
+ * C > 2 or r > 16 the STENCIL (cat_set_options changes them).  Errors:
+ * INVALID_ARG (H or W < 1, H or W > 2^31 - 256, H * pitch > 2^40, bad rule,
+ * unknown boundary), UNSUPPORTED (r > 16 with a periodic boundary), OOM,
+ * CUDA.                                                                     */
 CAT_API int cat_create(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary,
                cat_handle_t *out);
 
@@ -162,14 +174,20 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
 CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage,
                     int32_t steps_per_launch);
 
-/* Copies a grid into the instance's current buffer.  src holds H rows of W
- * bytes at `pitch` (>= W) bytes; it is device memory when src_on_device != 0,
- * else host memory (pageable or pinned).  Enqueued on `stream`; a pageable
- * host source is copied synchronously.  Errors: INVALID_ARG, CUDA.          */
+/* Copies a grid into the instance's current buffer: the state Lambda that the
+ * next step reads (Sec. IV-C, Alg. 1: the grid the ping-pong loop starts
+ * from).  src holds H rows of W bytes at `pitch` (>= W) bytes, states in
+ * [0, C); it is device memory when src_on_device != 0, else host memory
+ * (pageable or pinned).  Enqueued on `stream`; a pageable host source is
+ * copied synchronously.  The caller keeps ownership of src.  Errors:
+ * INVALID_ARG (NULL, pitch < W), CUDA.                                      */
 CAT_API int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src_on_device,
                   void *stream);
 
-/* Copies the current grid out (same layout rules as cat_set_state).          */
+/* Copies the current grid out: the state after the steps taken so far (the
+ * buffer the last step of the Sec. IV-C ping-pong wrote).  Same layout,
+ * ownership and error rules as cat_set_state; dst is written, H rows of W
+ * bytes at `pitch`.                                                          */
 CAT_API int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_device,
                   void *stream);
 
@@ -194,8 +212,13 @@ CAT_API int cat_state_ptr(cat_handle_t h, void **dptr, int64_t *pitch);
  * CUDA.                                                                     */
 CAT_API int cat_bind(cat_handle_t h, uint8_t *a, uint8_t *b, int64_t pitch);
 
-/* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`
- * (one kernel launch per step; the buffers swap after every step).          */
+/* Advances the instance by n_steps >= 0 synchronous LTL steps on `stream`:
+ * the host loop of Sec. IV-C (Alg. 1), one launch reading buffer A and
+ * writing buffer B, then the two swap (with steps_per_launch = k > 1, k steps
+ * per launch, the swap inside it).  Each step computes the band products of
+ * Sec. IV (Eqs. 1-2) and the rule of Sec. V-A for every cell.  Errors:
+ * INVALID_ARG (NULL, n_steps < 0), CUDA (launch failure); device-side
+ * timeouts are reported by cat_status.                                     */
 CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);
 
 /* Advances `count` independent instances by n_steps each.  The instances may
@@ -234,19 +257,29 @@ CAT_API int cat_status(cat_handle_t h, void *stream);
  * persistent tcgen05 launch and allocates nothing: the caller passes the input
  * and output buffers (device memory, e.g. from its own allocator), and the
  * table and work-list go into one fixed array compiled into the library
- * (753,792 bytes = about 736 KiB of device memory, held on every GPU that loads the library
- * until the process exits).
+ * (753,664 bytes = 736 KiB of device memory, held on every GPU that loads the
+ * library until the process exits).
  *
  *  - Limits: at most CAT_STATIC_MAX_GRIDS grids and CAT_STATIC_MAX_TILES tiles
  *    of 128 x 128 cells in total; larger batches get CAT_ERR_INVALID_ARG and
  *    nothing is launched.  Each grid: 1 <= H, W <= 4194176, pitch >= W and a
- *    multiple of 16 bytes, 16-byte aligned buffers, `in` != `out`.
+ *    multiple of 16 bytes, 16-byte aligned buffers, r <= 16, Moore
+ *    neighbourhood, zero boundary.
+ *  - Buffers: all grids advance in one launch, so a grid's `out` bytes (rows
+ *    0..H-1 at `pitch`, W bytes each) may overlap no other grid's `in` or
+ *    `out` and not its own `in`; inputs may share memory.  Overlaps are
+ *    rejected with CAT_ERR_INVALID_ARG.
  *  - dtype: CAT_DTYPE_FP8_E4M3 (or AUTO) or CAT_DTYPE_FP16.
- *  - d_status: optional device int32 that receives 0, or a non-zero code if a
- *    bounded device wait timed out; it is zeroed at the start of the call.
+ *  - d_status: required device int32 (NULL is CAT_ERR_INVALID_ARG).  It is
+ *    zeroed at the start of the call and receives a non-zero code if a
+ *    bounded device wait timed out, in which case the kernel skipped its
+ *    remaining tiles and `out` is incomplete.  The call itself returns before
+ *    the launch completes, so only d_status reports such a timeout.
+ *  - The table is staged from host memory that the next call reuses, so the
+ *    call must not be captured into a CUDA graph: on a capturing stream it
+ *    returns CAT_ERR_INVALID_ARG without enqueueing anything.
  *  - The first call on a device finds the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current.
  *  - Every call reuses the same array, which keeps the last call's contents.
  *    Calls whose launches overlap on the GPU (e.g. on two streams without an
  *    ordering between them) race on it: order them on one stream.
@@ -265,6 +298,19 @@ typedef struct cat_grid_desc {
 
 CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32_t count, int32_t dtype,
                                   int32_t *d_status, void *stream);
+
+/* Measurement: the dense tcgen05 MMA rate of the current GPU, the denominator
+ * of the roofline's tensor term (the paper has no counterpart; its cost model,
+ * Sec. IV-D, uses the vendor's peak).  Launches one CTA per SM, each issuing
+ * mmas_per_sm back-to-back MMAs of M = 128, N = 256 with zero operands in
+ * shared memory and f32 accumulators in tensor memory; dtype
+ * CAT_DTYPE_FP8_E4M3 (K = 32, kind::f8f6f4) or CAT_DTYPE_FP16 (K = 16,
+ * kind::f16).  The caller times the launch on `stream`; it performs
+ * SMs x mmas_per_sm x 2 x 128 x 256 x K flops.  d_status (device int32,
+ * required) receives a non-zero code if the bounded wait for the MMAs gave
+ * up; the caller zeroes it.  Errors: INVALID_ARG (mmas_per_sm outside
+ * [1, 2^30], NULL d_status), UNSUPPORTED (another dtype or device), CUDA.   */
+CAT_API int cat_tensor_probe(int32_t dtype, int64_t mmas_per_sm, int32_t *d_status, void *stream);
 
 /* Test hook for the failure-detection path; not needed in normal use.
  *   what = 1: value 1 makes the next tcgen05 launches wait on a barrier that

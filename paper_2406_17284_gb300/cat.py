@@ -36,7 +36,8 @@ KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MM
 
 EXPORTED = ["cat_create", "cat_create_ex", "cat_bind", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
             "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
-            "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static"]
+            "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static",
+            "cat_tensor_probe"]
 
 CAT_STATIC_MAX_GRIDS = 256
 CAT_STATIC_MAX_TILES = 65536
@@ -97,6 +98,7 @@ def load(path: str | None = None):
             "cat_last_error": [],
             "cat_version": [],
             "cat_batch_step_static": [ctypes.POINTER(cat_grid_desc_t), i32, i32, p, p],
+            "cat_tensor_probe": [i32, i64, p, p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -193,6 +195,12 @@ def cat_batch_step_static(descs: list, dtype: int = DTYPE_FP8_E4M3, status_ptr: 
     """One step of every grid in `descs` (cat_grid_desc_t) without device allocation."""
     arr = (cat_grid_desc_t * len(descs))(*descs)
     return load().cat_batch_step_static(arr, len(descs), dtype, status_ptr, _stream_ptr(stream))
+
+
+def cat_tensor_probe(dtype: int, mmas_per_sm: int, status_ptr: int, stream=None):
+    """Launches the dense tcgen05 MMA rate probe (flops per launch: SMs x
+    mmas_per_sm x 2 x 128 x 256 x K, K = 32 for FP8 e4m3, 16 for FP16)."""
+    _check(load().cat_tensor_probe(dtype, mmas_per_sm, status_ptr, _stream_ptr(stream)))
 
 
 def cat_version() -> str:

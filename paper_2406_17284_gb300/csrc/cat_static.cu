@@ -20,8 +20,8 @@ namespace {
 struct StaticScratch {
   cat::BatchInst inst[CAT_STATIC_MAX_GRIDS];
   cat::BatchTile tiles[CAT_STATIC_MAX_TILES];
-  int32_t status;
 };
+static_assert(sizeof(StaticScratch) == 753664, "the size include/cat.h states");
 
 // The scratch lives in device memory for as long as the library is loaded.
 // In host code `g_scratch` only names the symbol; its device address comes
@@ -69,6 +69,11 @@ int scratch_address(DeviceSlot **slot) {
   return CAT_OK;
 }
 
+// Bytes of grid memory a descriptor's buffer spans: rows 0 .. H-1 at `pitch`.
+uintptr_t span(int64_t H, int64_t W, int64_t pitch) { return (uintptr_t)((H - 1) * pitch + W); }
+
+bool overlap(uintptr_t a, uintptr_t na, uintptr_t b, uintptr_t nb) { return a < b + nb && b < a + na; }
+
 }  // namespace
 
 extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32_t count, int32_t dtype,
@@ -76,6 +81,7 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
   if (!grids || count < 1) return err(CAT_ERR_INVALID_ARG, "need at least one grid");
   if (count > CAT_STATIC_MAX_GRIDS)
     return err(CAT_ERR_INVALID_ARG, "%lld grids exceed the static limit of %lld", count, CAT_STATIC_MAX_GRIDS);
+  if (!d_status) return err(CAT_ERR_INVALID_ARG, "d_status is NULL: a timed-out launch could not be reported");
   if (dtype == CAT_DTYPE_AUTO) dtype = CAT_DTYPE_FP8_E4M3;
   if (dtype != CAT_DTYPE_FP8_E4M3 && dtype != CAT_DTYPE_FP16)
     return err(CAT_ERR_UNSUPPORTED, "dtype %lld: only FP8 and FP16 operands are served here", dtype);
@@ -100,13 +106,35 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
   if (n_tiles > CAT_STATIC_MAX_TILES)
     return err(CAT_ERR_INVALID_ARG, "%lld tiles of 128 x 128 cells exceed the static limit of %lld", n_tiles,
                CAT_STATIC_MAX_TILES);
+  // one persistent launch steps every grid at once: a grid's output may share
+  // no byte with another grid's input or output (inputs may share bytes)
+  for (int32_t i = 0; i < count; ++i) {
+    const cat_grid_desc_t &g = grids[i];
+    const uintptr_t o = (uintptr_t)g.out, no = span(g.H, g.W, g.pitch);
+    for (int32_t j = 0; j < count; ++j) {
+      const cat_grid_desc_t &k = grids[j];
+      const uintptr_t nk = span(k.H, k.W, k.pitch);
+      if (overlap(o, no, (uintptr_t)k.in, nk) || (j != i && overlap(o, no, (uintptr_t)k.out, nk)))
+        return err(CAT_ERR_INVALID_ARG, "grid %lld writes memory that grid %lld also uses", i, j);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    // the table is staged from host memory that the next call overwrites, so
+    // a captured copy would replay stale contents: refuse capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return err(CAT_ERR_CUDA, "cudaStreamIsCapturing failed (%lld)", (long long)e);
+    if (cs != cudaStreamCaptureStatusNone)
+      return err(CAT_ERR_INVALID_ARG, "cat_batch_step_static may not be captured into a CUDA graph");
+  }
 
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceSlot *slot = nullptr;
   int rc = scratch_address(&slot);
   if (rc) return rc;
   StaticScratch &h = g_host_stage;
-  int32_t *status = d_status ? d_status : &slot->ptr->status;
+  int32_t *status = d_status;
   int64_t t = 0;
   // work-list ordered by radius (the kernel rebuilds its band when r changes)
   for (int r = 1; r <= 16; ++r)
@@ -131,7 +159,6 @@ extern "C" CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32
     I.cur = 0;
     I.err = status;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(slot->ptr->inst, h.inst, sizeof(cat::BatchInst) * count, cudaMemcpyHostToDevice, s);

@@ -80,3 +80,10 @@ def test_null_handles_rejected(lib):
     assert lib.cat_destroy(None) == cat.CAT_OK
     assert lib.cat_batch_step(None, 1, 1, None) == cat.CAT_ERR_INVALID_ARG
     assert lib.cat_bind(None, None, None, 16) == cat.CAT_ERR_INVALID_ARG
+
+
+def test_tensor_probe_rejects_bad_arguments_without_gpu(lib):
+    assert lib.cat_tensor_probe(cat.DTYPE_INT8, 16, 1024, None) == cat.CAT_ERR_UNSUPPORTED
+    assert lib.cat_tensor_probe(cat.DTYPE_FP8_E4M3, 0, 1024, None) == cat.CAT_ERR_INVALID_ARG
+    assert lib.cat_tensor_probe(cat.DTYPE_FP16, 16, None, None) == cat.CAT_ERR_INVALID_ARG
+    assert b"d_status" in lib.cat_last_error()

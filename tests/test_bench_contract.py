@@ -7,11 +7,13 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
+    t0 = time.perf_counter()
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
                           "--cpu-sample", "256", "--radii", "1,2"],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
@@ -29,3 +31,5 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["radii"] == [1, 2]
+    # ms_per_step is the measured time of a step, so the timed steps fit in the run
+    assert d["ms_per_step"] * d["steps"] / 1000.0 < time.perf_counter() - t0
