@@ -365,12 +365,21 @@ def measure_multistate(args, torch, cat, inputs, stream):
     rule = inputs.MULTISTATE_R10_C16
     n = args.multistate_size
     out = {"workload": f"{n}x{n} and 256 x 2048x2048, states uniform over 0..15, R10 C16 M1 S150..260 B150..200"}
+    init = inputs.uniform_states(n, n, 16, 4915)
     g = cat.Grid(n, n, rule, kernel="tcgen05", dtype="fp8")
-    g.set_state(inputs.uniform_states(n, n, 16, 4915))
+    g.set_state(init)
     g.step(1, stream)
     t = time_launches(torch, lambda: g.step(1, stream), 4, stream)
     out["single_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
     g.close()
+    # the same grid stored four bits per cell (1 byte of state traffic per update)
+    g = cat.Grid(n, n, rule, kernel="tcgen05", dtype="fp8", storage=cat.STORE_NIB4)
+    g.set_state(init)
+    g.step(1, stream)
+    t = time_launches(torch, lambda: g.step(1, stream), 4, stream)
+    out["single_nib4_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
+    g.close()
+    del init
     grids = [cat.Grid(2048, 2048, rule, kernel="tcgen05", dtype="fp8") for _ in range(256)]
     for i, gg in enumerate(grids):
         gg.set_state(inputs.uniform_states(2048, 2048, 16, 5000 + i))
@@ -466,18 +475,22 @@ def measure_multistep(torch, cat, inputs, stream, steps=64):
 
 
 def measure_wide(args, torch, cat, inputs, stream, d_init):
-    """Radii beyond 16 on the headline's grid: the FP16 fragment kernel with a second
-    halo fragment (five band fragments per reduction, FP32 step-2 accumulation)."""
+    """Radii beyond 16 on the headline's grid: the tcgen05 kernel on 96 x 96 tiles
+    (32-cell halo, e4m3 digits against a band of ones and a band of 16s, f32 pass 2),
+    and the FP16 fragment kernel with a second halo fragment (five band fragments
+    per reduction, FP32 step-2 accumulation)."""
     n = args.size
-    out = {"workload": f"{n}x{n} bernoulli0.5, scaled rule C2 M1, FP16 fragment kernel (r > 16)"}
-    for r in (17, 24, 32):
-        g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="mma_sync", dtype="fp16")
-        g.set_state(d_init)
-        g.step(1, stream)
-        t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
-        assert g.status() == cat.CAT_OK
-        out[f"r{r}_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
-        g.close()
+    out = {"workload": f"{n}x{n} bernoulli0.5, scaled rule C2 M1, r > 16: tcgen05 96x96 tile (fp8) "
+                       "and the FP16 fragment kernel", "kernel": "ltl_wide_kernel"}
+    for kern, dt, key in (("tcgen05", "fp8", "tcgen05_fp8"), ("mma_sync", "fp16", "fragment_fp16")):
+        for r in (17, 24, 32):
+            g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel=kern, dtype=dt)
+            g.set_state(d_init)
+            g.step(1, stream)
+            t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
+            assert g.status() == cat.CAT_OK
+            out[f"{key}_r{r}_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
+            g.close()
     return out
 
 
@@ -494,9 +507,20 @@ def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
     per_r = measure_sweep(torch, cat, stream, grids, n)
     ms = sum(per_r.values())
     achieved = 0.25 * n * n * len(RADII) / (ms / 1000.0) / 1e9
+    # the bit-sliced CUDA-core kernel on the same packed grids, r <= 3
+    sliced = {}
+    for r in [r for r in RADII if r <= 3]:
+        g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="bitslice", storage=cat.STORE_BIT1)
+        g.set_state(d_init)
+        g.step(2, stream)
+        t = time_launches(torch, lambda: g.step(1, stream), 5, stream)
+        assert g.status() == cat.CAT_OK
+        sliced[str(r)] = n * n / (statistics.median(t) / 1000.0)
+        g.close()
     return {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5, one bit per cell, fp8",
             "cell_updates_per_s": n * n * len(RADII) / (ms / 1000.0),
             "per_r_cell_updates_per_s": {str(r): n * n / (t / 1000.0) for r, t in per_r.items()},
+            "bitslice_cell_updates_per_s": sliced,
             "bytes_per_cell": 0.25, "achieved_gbs": achieved, "hbm_frac": achieved / hbm,
             "traffic_bytes_per_launch": recorded_traffic("bits", n * n), "kernel": "ltl_bits_kernel"}
 
@@ -631,7 +655,7 @@ def run_cat(args, rank, world, local):
     comps = {}
     if not args.no_compare and rank == 0:
         variants = [("tcgen05", "fp16" if args.dtype == "fp8" else "fp8"), ("mma_sync", "fp16"),
-                    ("mma_sync", "int8"), ("stencil", "auto")]
+                    ("mma_sync", "int8"), ("stencil", "auto"), ("runsum", "auto")]
         for kern, dt in variants:
             row = {}
             for r in RADII:
@@ -687,6 +711,9 @@ def run_cat(args, rank, world, local):
         batched["roofline"].update({k: roof(batched[k], 2.0, None, hbm)
                                     for k in ["fp16_paper_mma_sync_per_grid"] if batched.get(k)})
     roofs(multistate, ["single_cell_updates_per_s", "batch_256x2048_cell_updates_per_s"], 2.0, e4m3_peak)
+    if multistate and multistate.get("single_nib4_cell_updates_per_s"):
+        multistate["roofline"]["single_nib4_cell_updates_per_s"] = roof(
+            multistate["single_nib4_cell_updates_per_s"], 1.0, e4m3_peak, hbm)
     roofs(periodic, [k for k in (periodic or {}) if k.endswith("_per_s")], 2.0, e4m3_peak)
     roofs(bits, ["cell_updates_per_s"], 0.25, e4m3_peak)
     roofs(vn, ["cell_updates_per_s"], 2.0, e4m3_peak)
@@ -724,6 +751,11 @@ def run_cat(args, rank, world, local):
             "per_r_cell_updates_per_s": per_r_rate,
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
             "comparators_roofline_frac": comp_roofs,
+            # the headline kernel's rate over the fastest CUDA-core kernel (direct
+            # stencil or separable running sums) at each r
+            "tensor_core_over_best_cuda_core": {
+                str(r): per_r_rate[str(r)] / max(comps[k][r] for k in ("stencil/auto", "runsum/auto") if k in comps)
+                for r in RADII} if "runsum/auto" in comps else None,
             "batched": batched,
             "multistate": multistate,
             "periodic": periodic,

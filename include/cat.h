@@ -53,10 +53,11 @@ extern "C" {
 
 /* LTL rule in the R C M S B N notation of Sec. V-A (Table IV lists instances).
  *   r      neighbourhood radius, 1 <= r <= 32.  Up to 16 (the fragment size,
- *          Sec. IV-A) every kernel serves it; 17..32 (the extension with a
- *          second halo fragment that Sec. VII describes) is served by the FP16
- *          fragment kernel (MMA_SYNC, Moore) and the stencil, with uint8
- *          storage and the zero boundary; CAT_KERNEL_AUTO picks them.
+ *          Sec. IV-A) every kernel serves it; 17..32 (the extension to a
+ *          second halo fragment that Sec. VII describes) is served with uint8
+ *          storage and the zero boundary by TCGEN05 on 96 x 96 tiles (FP8,
+ *          C = 2, Moore; CAT_KERNEL_AUTO picks it), by the FP16 fragment
+ *          kernel (MMA_SYNC, Moore, every C) and by the stencil.
  *   C      number of states, 2 <= C <= 255
  *   M      1: the centre cell counts towards k; 0: it does not
  *   s1,s2  survival range for state-1 cells (inclusive; s1 > s2 means empty)
@@ -87,7 +88,9 @@ enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
  *   FP8_E4M3  a state byte 0x01 read as e4m3 is 2^-9, so the raw bytes are the
  *             pass-1 operand; H * 2^-9 is an e4m3 number while H <= 15
  *             (2r+1 <= 15).  Beyond that the TCGEN05 kernel passes H to the
- *             second product as f16 operands.
+ *             second product as f16 operands on 128 x 128 tiles, and on the
+ *             96 x 96 tile (H <= 65) as two e4m3 digits, H & 15 against the
+ *             band and H >> 4 against a band of 16s (f32 accumulation).
  *   INT8      H <= 65 < 127; served by MMA_SYNC (sm_103a has no tcgen05 kind::i8).
  *   FP4_E2M1  not served by this build (UNSUPPORTED).                         */
 enum {
@@ -104,26 +107,50 @@ enum {
  *         bit x % 8 of byte x / 8 (lowest x in the lowest bit), so a row takes
  *         ceil(W / 8) bytes and the bits past W in the last byte stay 0.  An
  *         eighth of the HBM traffic of U8.  Stepped by the TCGEN05 kernel on
- *         FP8 operands with the zero boundary; cat_batch_step advances BIT1
+ *         FP8 operands, or by BITSLICE for r <= 3, with the zero boundary
+ *         (Moore neighbourhood); cat_batch_step advances BIT1
  *         instances one launch per instance and step.  The state is still
  *         passed in and out one byte per cell (cat_set_state/cat_get_state
- *         convert on the device); cat_state_ptr exposes the packed rows.      */
-enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1 };
+ *         convert on the device); cat_state_ptr exposes the packed rows.
+ *   NIB4  four bits per cell, for rules with C <= 16 (the multi-state rules
+ *         of the Generations reading): cell x of a row is nibble x % 2 of
+ *         byte x / 2 (even x in the low nibble), so a row takes ceil(W / 2)
+ *         bytes and the nibble past an odd W stays 0.  Half the HBM traffic
+ *         of U8.  Stepped by the TCGEN05 kernel on FP8 operands (the window
+ *         unpacked to state-1 flags in shared memory), r <= 16, Moore, the
+ *         zero boundary, one step per launch; cat_batch_step advances NIB4
+ *         instances one launch per instance and step.  State in and out as
+ *         with BIT1.                                                        */
+enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1, CAT_STORE_NIB4 = 2 };
 
 /* Which kernel advances the grid.
- *   TCGEN05   TMA-staged haloed 128x128 tiles, both band products on the
- *             5th-generation tensor cores (tcgen05.mma, TMEM accumulators),
- *             transition fused into the epilogue (FP16 or FP8 operands).
+ *   TCGEN05   TMA-staged haloed 128x128 tiles (96x96 with a 32-cell halo for
+ *             r > 16), both band products on the 5th-generation tensor cores
+ *             (tcgen05.mma, TMEM accumulators), transition fused into the
+ *             epilogue (FP16 or FP8 operands).
  *   MMA_SYNC  the paper's own fragment scheme (Alg. 1: three 16x16 band
  *             fragments, 6 MMAs per fragment) on warp-level mma.sync
  *             (FP16 operands, or INT8 operands for CAT_DTYPE_INT8).
  *   STENCIL   classical shared-memory CUDA-core stencil (the out-halo SHARED
- *             design of Sec. V-A, Table V), one (2r+1)^2 loop per cell.      */
+ *             design of Sec. V-A, Table V), one (2r+1)^2 loop per cell.
+ *   BITSLICE  bit-sliced CUDA-core kernel on one-bit storage for r <= 3, the
+ *             packed-cell regime where Sec. V-B finds packing faster than
+ *             tensor cores: the counts of 32 cells per 32-bit word are added
+ *             as bit planes by bitwise full adders, and the rule is a
+ *             bit-serial range comparison (CAT_STORE_BIT1, C = 2, Moore, zero
+ *             boundary; no operand dtype).
+ *   RUNSUM    separable running-sum CUDA-core kernel, O(1) work per cell in
+ *             r: vertical box sums as running sums down columns (four cells
+ *             per 32-bit word), then horizontal running sums along rows
+ *             (Moore neighbourhood, every C, uint8 storage, zero boundary,
+ *             r <= 32): the strongest CUDA-core reference point.           */
 enum {
   CAT_KERNEL_AUTO = 0,
   CAT_KERNEL_TCGEN05 = 1,
   CAT_KERNEL_MMA_SYNC = 2,
-  CAT_KERNEL_STENCIL = 3
+  CAT_KERNEL_STENCIL = 3,
+  CAT_KERNEL_BITSLICE = 4,
+  CAT_KERNEL_RUNSUM = 5
 };
 
 typedef struct cat_instance *cat_handle_t;
@@ -137,9 +164,9 @@ typedef struct cat_instance *cat_handle_t;
  * 16), refreshed by a small kernel before every step, and is stepped by the
  * tcgen05 kernel only.  The state is all zero until cat_set_state.  The
  * instance owns its buffers; cat_destroy frees them.  Uses the current CUDA
- * device.  The kernel defaults to TCGEN05 with FP8 operands; r > 16 selects
- * MMA_SYNC with FP16 operands, and the simplified von Neumann cross with
- * C > 2 or r > 16 the STENCIL (cat_set_options changes them).  Errors:
+ * device.  The kernel defaults to TCGEN05 with FP8 operands; r > 16 with C > 2
+ * selects MMA_SYNC with FP16 operands, and the simplified von Neumann cross
+ * with C > 2 or r > 16 the STENCIL (cat_set_options changes them).  Errors:
  * INVALID_ARG (H or W < 1, H or W > 2^31 - 256, H * pitch > 2^40, bad rule,
  * unknown boundary), UNSUPPORTED (r > 16 with a periodic boundary), OOM,
  * CUDA.                                                                     */
@@ -160,7 +187,8 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * TCGEN05, FP16 for MMA_SYNC; instances start with CAT_STORE_U8).  A change
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).
- * CAT_STORE_BIT1 needs C = 2, the zero boundary, TCGEN05 and FP8_E4M3.
+ * CAT_STORE_BIT1 needs C = 2, the zero boundary and TCGEN05 with FP8_E4M3,
+ * or BITSLICE (r <= 3).
  * steps_per_launch = k > 1 makes cat_step run k steps per kernel launch: one
  * cooperative launch (all CTAs resident, one per SM) whose CTAs meet on a
  * grid-wide barrier between steps, so small grids stop paying a launch per
@@ -173,6 +201,60 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * UNSUPPORTED or OOM the instance keeps its previous options and state.     */
 CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage,
                     int32_t steps_per_launch);
+
+/* Tile shape and window of the TCGEN05 Moore kernel (the ty, tx tile options;
+ * the step's results do not depend on them, only its speed).
+ *   ty x tx  0 x 0: chosen by the radius (128 x 128 for r <= 16, else 96 x 96);
+ *            128 x 128: the tile of a 160 x 160 window with a 16-cell halo
+ *            (r <= 16); 96 x 96: the tile of the same window with a 32-cell
+ *            halo (any r <= 32; FP8 operands, C = 2, uint8 storage, the zero
+ *            boundary, one step per launch).
+ *   window_rows  0: chosen by the rule (144 for FP8 operands, C = 2, r <= 7,
+ *            else 160); 144: the short window (128 x 128 tile, FP8, C = 2,
+ *            r <= 7, uint8 storage); 160: the full window.
+ * The autotuner in the Python package drives this call.  Later changes of
+ * kernel, dtype or storage that a chosen tile does not serve are rejected by
+ * cat_set_options.  Errors: INVALID_ARG (other shapes), UNSUPPORTED (a shape
+ * the instance's kernel, dtype, storage, boundary or rule does not serve). */
+CAT_API int cat_set_tile(cat_handle_t h, int32_t ty, int32_t tx, int32_t window_rows);
+
+/* The options in force: kernel, operand dtype (CAT_DTYPE_AUTO for kernels
+ * without one), storage, steps per launch, and for the TCGEN05 Moore kernel
+ * the tile side (128 or 96) and window rows (144 or 160; 0 for the 96 x 96
+ * tile); 0 where they do not apply.  Any pointer may be NULL.  Errors:
+ * INVALID_ARG (NULL handle).                                                */
+CAT_API int cat_get_options(cat_handle_t h, int32_t *kernel, int32_t *dtype, int32_t *storage,
+                            int32_t *steps_per_launch, int32_t *tile, int32_t *window_rows);
+
+/* Autotuner (the paper tunes its tile shape by hand, Sec. V-B; every
+ * candidate computes the same states, so only speed is at stake).  Times
+ * every configuration the instance can run -- kernel x operand dtype x tile
+ * shape x window x steps per launch (1, 4, 16), keeping its storage -- with
+ * n_steps steps each from its current state (CUDA events on `stream`), then
+ * applies the fastest and restores the state.  The choice is appended to the
+ * JSON-lines file cache_path (NULL: no file), one object per line:
+ *   {"key": "H=.. W=.. r=.. C=.. nbhd=.. boundary=.. storage=.. gpu=<name>/<SMs>",
+ *    "kernel": k, "dtype": d, "tile": t, "window": w, "steps_per_launch": s,
+ *    "cell_updates_per_s": v}
+ * and when the file already holds an entry for the instance, that entry is
+ * applied without timing (unless flags has CAT_TUNE_REMEASURE).  With the
+ * environment variable CAT_AUTOTUNE_CACHE naming such a file,
+ * cat_set_options(CAT_KERNEL_AUTO, ...) takes the cached choice (kernel,
+ * dtype, steps per launch, tile, window) in place of its fixed rule.
+ * Synchronises `stream`; allocates a temporary copy of the state.  Errors:
+ * INVALID_ARG, UNSUPPORTED (no candidate ran), OOM/CUDA.                    */
+#define CAT_TUNE_REMEASURE 1 /* ignore a cached entry and time again         */
+#define CAT_TUNE_NO_WRITE 2  /* do not append the choice to the cache file   */
+CAT_API int cat_autotune(cat_handle_t h, int32_t n_steps, const char *cache_path, int32_t flags, void *stream);
+
+/* Autotuner for a batch: one configuration for all instances (a batched
+ * launch shares kernel and dtype) -- TCGEN05 with FP8 or FP16 operands, the
+ * window chosen by the rule or the full one -- each timed over n_steps steps
+ * of cat_batch_step after one untimed call; applies the fastest, restores
+ * every state and reports its dtype in *chosen_dtype (may be NULL).
+ * Synchronises `stream`.  Errors: as cat_batch_step, UNSUPPORTED.           */
+CAT_API int cat_autotune_batch(const cat_handle_t *hs, int32_t count, int32_t n_steps, int32_t *chosen_dtype,
+                               void *stream);
 
 /* Copies a grid into the instance's current buffer: the state Lambda that the
  * next step reads (Sec. IV-C, Alg. 1: the grid the ping-pong loop starts

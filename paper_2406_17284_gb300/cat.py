@@ -26,18 +26,21 @@ BOUNDARY_ZERO = 0
 BOUNDARY_PERIODIC = 1
 
 DTYPE_AUTO, DTYPE_FP16, DTYPE_FP8_E4M3, DTYPE_INT8, DTYPE_FP4_E2M1 = 0, 1, 2, 3, 4
-STORE_U8, STORE_BIT1 = 0, 1
-KERNEL_AUTO, KERNEL_TCGEN05, KERNEL_MMA_SYNC, KERNEL_STENCIL = 0, 1, 2, 3
+STORE_U8, STORE_BIT1, STORE_NIB4 = 0, 1, 2
+KERNEL_AUTO, KERNEL_TCGEN05, KERNEL_MMA_SYNC, KERNEL_STENCIL, KERNEL_BITSLICE, KERNEL_RUNSUM = 0, 1, 2, 3, 4, 5
 
 DTYPES = {"auto": DTYPE_AUTO, "fp16": DTYPE_FP16, "fp8": DTYPE_FP8_E4M3, "int8": DTYPE_INT8,
           "fp4": DTYPE_FP4_E2M1}
 KERNELS = {"auto": KERNEL_AUTO, "tcgen05": KERNEL_TCGEN05, "mma_sync": KERNEL_MMA_SYNC,
-           "stencil": KERNEL_STENCIL}
+           "stencil": KERNEL_STENCIL, "bitslice": KERNEL_BITSLICE, "runsum": KERNEL_RUNSUM}
 
-EXPORTED = ["cat_create", "cat_create_ex", "cat_bind", "cat_set_options", "cat_set_state", "cat_get_state", "cat_state_ptr",
+EXPORTED = ["cat_create", "cat_create_ex", "cat_bind", "cat_set_options", "cat_set_tile", "cat_set_state", "cat_get_state", "cat_state_ptr",
             "cat_step", "cat_batch_step", "cat_box_sums", "cat_status", "cat_debug_control",
             "cat_destroy", "cat_last_error", "cat_version", "cat_batch_step_static",
-            "cat_tensor_probe"]
+            "cat_tensor_probe", "cat_get_options", "cat_autotune", "cat_autotune_batch"]
+
+CAT_TUNE_REMEASURE = 1
+CAT_TUNE_NO_WRITE = 2
 
 CAT_STATIC_MAX_GRIDS = 256
 CAT_STATIC_MAX_TILES = 65536
@@ -85,6 +88,7 @@ def load(path: str | None = None):
             "cat_create": [i64, i64, ctypes.POINTER(cat_rule_t), i32, ctypes.POINTER(ctypes.c_void_p)],
             "cat_create_ex": [i64, i64, ctypes.POINTER(cat_rule_t), i32, i32, ctypes.POINTER(ctypes.c_void_p)],
             "cat_set_options": [h, i32, i32, i32, i32],
+            "cat_set_tile": [h, i32, i32, i32],
             "cat_set_state": [h, p, i64, i32, p],
             "cat_get_state": [h, p, i64, i32, p],
             "cat_state_ptr": [h, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)],
@@ -99,6 +103,9 @@ def load(path: str | None = None):
             "cat_version": [],
             "cat_batch_step_static": [ctypes.POINTER(cat_grid_desc_t), i32, i32, p, p],
             "cat_tensor_probe": [i32, i64, p, p],
+            "cat_get_options": [h] + [ctypes.POINTER(ctypes.c_int32)] * 6,
+            "cat_autotune": [h, i32, ctypes.c_char_p, i32, p],
+            "cat_autotune_batch": [ctypes.POINTER(ctypes.c_void_p), i32, i32, ctypes.POINTER(ctypes.c_int32), p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -145,6 +152,10 @@ def cat_create_ex(H: int, W: int, rule: cat_rule_t, boundary: int = BOUNDARY_ZER
 def cat_set_options(h: int, kernel: int = KERNEL_AUTO, dtype: int = DTYPE_AUTO, storage: int = STORE_U8,
                     steps_per_launch: int = 1):
     _check(load().cat_set_options(h, kernel, dtype, storage, steps_per_launch))
+
+
+def cat_set_tile(h: int, ty: int = 0, tx: int = 0, window_rows: int = 0):
+    _check(load().cat_set_tile(h, ty, tx, window_rows))
 
 
 def cat_set_state(h: int, src_ptr: int, pitch: int, on_device: bool, stream=None):
@@ -203,6 +214,24 @@ def cat_tensor_probe(dtype: int, mmas_per_sm: int, status_ptr: int, stream=None)
     _check(load().cat_tensor_probe(dtype, mmas_per_sm, status_ptr, _stream_ptr(stream)))
 
 
+def cat_get_options(h: int) -> dict:
+    v = [ctypes.c_int32() for _ in range(6)]
+    _check(load().cat_get_options(h, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("kernel", "dtype", "storage", "steps_per_launch", "tile", "window"), (x.value for x in v)))
+
+
+def cat_autotune(h: int, n_steps: int = 8, cache_path: str | None = None, flags: int = 0, stream=None):
+    _check(load().cat_autotune(h, n_steps, cache_path.encode() if cache_path else None, flags,
+                               _stream_ptr(stream)))
+
+
+def cat_autotune_batch(handles: list[int], n_steps: int = 4, stream=None) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    d = ctypes.c_int32()
+    _check(load().cat_autotune_batch(arr, len(handles), n_steps, ctypes.byref(d), _stream_ptr(stream)))
+    return d.value
+
+
 def cat_version() -> str:
     return load().cat_version().decode()
 
@@ -212,7 +241,8 @@ class Grid:
     """One LTL instance: owns a cat handle; state in/out as numpy or torch tensors."""
 
     def __init__(self, H: int, W: int, rule: dict, kernel: str = "tcgen05", dtype: str = "fp8",
-                 boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8, steps_per_launch: int = 1):
+                 boundary: int = BOUNDARY_ZERO, storage: int = STORE_U8, steps_per_launch: int = 1,
+                 tile: int = 0, window: int = 0):
         self.H, self.W = int(H), int(W)
         self.rule = dict(rule)
         self.storage = int(storage)
@@ -222,6 +252,8 @@ class Grid:
                                     boundary, self.storage)
         try:
             cat_set_options(self.handle, KERNELS[kernel], DTYPES[dtype], self.storage, steps_per_launch)
+            if tile or window:
+                cat_set_tile(self.handle, tile, tile, window)
         except Exception:
             cat_destroy(self.handle)
             self.handle = None   # __del__ must not free it again
@@ -260,14 +292,15 @@ class Grid:
 
     def state_tensor(self):
         """Zero-copy torch view of the current device buffer (H x pitch, uint8):
-        H x W cells, or H x ceil(W / 8) packed bytes with one-bit storage."""
+        H x W cells, or H x ceil(W / 8) / ceil(W / 2) packed bytes with one- /
+        four-bit storage."""
         import torch
         ptr, pitch = cat_state_ptr(self.handle)
 
         class _Arr:
             __cuda_array_interface__ = {"shape": (self.H, pitch), "typestr": "|u1",
                                         "data": (ptr, False), "version": 3}
-        cols = (self.W + 7) // 8 if self.storage == STORE_BIT1 else self.W
+        cols = {STORE_BIT1: (self.W + 7) // 8, STORE_NIB4: (self.W + 1) // 2}.get(self.storage, self.W)
         return torch.as_tensor(_Arr(), device="cuda")[:, :cols]
 
     def step(self, n_steps: int = 1, stream=None):

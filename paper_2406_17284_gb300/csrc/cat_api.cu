@@ -89,8 +89,11 @@ struct cat_instance {
   int cur = 0;
   int32_t *d_err = nullptr;
   // per buffer: window boxes 128 x 160 and 32 x 160, the 128 x 128 tile box,
-  // and the window boxes of the short-window kernel, 128 x 144 and 32 x 144
-  CUtensorMap maps[2][5];
+  // the window boxes of the short-window kernel, 128 x 144 and 32 x 144, and
+  // the 96 x 96 tile box (no swizzle) of the wide-tile kernel
+  CUtensorMap maps[2][6];
+  int32_t tile = 0;     // cat_set_tile: 0 chosen by the radius, 128 or 96
+  int32_t window = 0;   // cat_set_tile: 0 chosen by the rule, 144 or 160
   DeviceInfo dev;
   int32_t inject = 0;
   uint64_t timeout_ns = 2000000000ull;
@@ -149,13 +152,23 @@ int make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitch, ui
 }
 
 int build_maps(cat_instance *h) {
+  if (h->storage == CAT_STORE_NIB4) {  // packed rows: 96 x 160-byte windows, 64 x 128-byte tiles (64B swizzle)
+    for (int b = 0; b < 2; ++b) {
+      int rc;
+      const int64_t wb = (h->W + 1) / 2;
+      if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, wb, h->pitch, 96, 160, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+      if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, wb, h->pitch, 64, 128, CU_TENSOR_MAP_SWIZZLE_64B))) return rc;
+      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][0];
+    }
+    return CAT_OK;
+  }
   if (h->storage == CAT_STORE_BIT1) {  // packed rows: 48 x 160-byte windows, 16 x 128-byte tiles
     for (int b = 0; b < 2; ++b) {
       int rc;
       const int64_t wb = (h->W + 7) / 8;
       if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, wb, h->pitch, 48, 160, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
       if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, wb, h->pitch, 16, 128, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
-      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][0];
+      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][0];
     }
     return CAT_OK;
   }
@@ -168,14 +181,23 @@ int build_maps(cat_instance *h) {
     if ((rc = make_map(&h->maps[b][2], h->buf[b], H, W, h->pitch, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
     if ((rc = make_map(&h->maps[b][3], h->buf[b], H, W, h->pitch, 128, 144, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
     if ((rc = make_map(&h->maps[b][4], h->buf[b], H, W, h->pitch, 32, 144, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    if ((rc = make_map(&h->maps[b][5], h->buf[b], H, W, h->pitch, 96, 96, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
   }
   return CAT_OK;
 }
 
+// The wide-tile kernel (96 x 96 tiles, a 32-cell halo) serves radii above 16
+// on tcgen05, and any radius when cat_set_tile asks for it.
+bool wide_tile(const cat_instance *h) {
+  return h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' && (h->rule.r > 16 || h->tile == 96);
+}
+
 // The short-window kernel serves FP8 operands on two-state rules with r <= 7
-// (pass 2 then runs on e4m3, and 128 + 2r window rows fit in 144).
+// (pass 2 then runs on e4m3, and 128 + 2r window rows fit in 144), unless
+// cat_set_tile asked for the 160-row window.
 bool short_window(const cat_instance *h) {
-  return h->kernel == CAT_KERNEL_TCGEN05 && h->dtype == CAT_DTYPE_FP8_E4M3 && h->rule.C == 2 && h->rule.r <= 7;
+  return h->kernel == CAT_KERNEL_TCGEN05 && h->dtype == CAT_DTYPE_FP8_E4M3 && h->rule.C == 2 && h->rule.r <= 7 &&
+         h->window != 160 && !wide_tile(h);
 }
 
 // n_steps steps of instance h from buffer `in` (into buffer 1 - in after an
@@ -193,7 +215,9 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.ox = p.oy = h->ghost;
     const bool vn = h->rule.nbhd == 'N';
     const bool bits = h->storage == CAT_STORE_BIT1;
-    const bool sw = !vn && !bits && short_window(h);
+    const bool nib = h->storage == CAT_STORE_NIB4;
+    const bool sw = !vn && !bits && !nib && short_window(h);
+    const bool wide = !vn && wide_tile(h);
     p.map_in_a = h->maps[in][sw ? 3 : 0];
     p.map_in_b = h->maps[in][sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
@@ -207,10 +231,15 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
       p.gbar = reinterpret_cast<uint32_t *>(h->d_err) + 1;
       p.gbar_base = h->gbar_count;
     }
+    const int ts = wide ? 96 : 128;
+    if (wide) {   // 96 x 96 centre and output tiles
+      p.map_out = h->maps[1 - in][5];
+      p.map_ctr = h->maps[in][5];
+    }
     p.H = (int32_t)h->H;
     p.W = (int32_t)h->W;
-    p.tiles_x = (int32_t)((h->W + 127) / 128);
-    p.n_tiles = p.tiles_x * (int32_t)((h->H + 127) / 128);
+    p.tiles_x = (int32_t)((h->W + ts - 1) / ts);
+    p.n_tiles = p.tiles_x * (int32_t)((h->H + ts - 1) / ts);
     p.rule = h->rd;
     p.err = h->d_err;
     p.sums = sums;
@@ -218,7 +247,10 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.timeout_ns = h->timeout_ns;
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
-    e = vn ? cat::vn_launch(p, grid, s) : cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
+    e = vn ? cat::vn_launch(p, grid, s)
+           : wide ? cat::wide_launch(p, grid, s)
+           : nib  ? cat::nib_launch(p, grid, s)
+                  : cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
     if (e == cudaSuccess && n_steps > 1) h->gbar_count += (uint32_t)grid * (uint32_t)(n_steps - 1);
   } else {
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
@@ -232,7 +264,12 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.rule = h->rd;
     p.sums = sums;
     p.sums_ld = sums_ld;
-    e = h->kernel == CAT_KERNEL_MMA_SYNC ? cat::mma_launch(p, h->dtype, s) : cat::stencil_launch(p, s);
+    if (h->kernel == CAT_KERNEL_BITSLICE)
+      e = cat::swar_launch(h->buf[in], h->buf[1 - in], h->pitch, h->H, h->W, h->rd, sums, sums_ld, s);
+    else if (h->kernel == CAT_KERNEL_RUNSUM)
+      e = cat::runsum_launch(p, s);
+    else
+      e = h->kernel == CAT_KERNEL_MMA_SYNC ? cat::mma_launch(p, h->dtype, s) : cat::stencil_launch(p, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return CAT_OK;
@@ -371,6 +408,20 @@ int host_make_map(CUtensorMap *m, void *base, int64_t H, int64_t W, int64_t pitc
   return make_map(m, base, H, W, pitch, box_x, box_y,
                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
+int host_instance_info(cat_handle_t h, InstanceInfo *f) {
+  if (!h || !f) return fail(CAT_ERR_INVALID_ARG, "NULL handle");
+  f->H = h->H;
+  f->W = h->W;
+  f->rule = h->rule;
+  f->boundary = h->boundary;
+  f->storage = h->storage;
+  f->kernel = h->kernel;
+  f->dtype = h->dtype;
+  f->tile = h->tile;
+  f->window = h->window;
+  f->steps_per_launch = h->steps_per_launch;
+  return CAT_OK;
+}
 }  // namespace cat
 
 namespace {
@@ -379,20 +430,49 @@ namespace {
 // on its way to or from one-bit storage (64 MiB at most).
 int64_t chunk_rows(int64_t W) { return std::max<int64_t>(1, std::min<int64_t>(4096, (64ll << 20) / W)); }
 
-// Reallocates the state of h in `storage`, converting the current grid.
+int64_t storage_pitch(int32_t storage, int64_t W) {
+  return storage == CAT_STORE_BIT1 ? round_up((W + 7) / 8, 16) : storage == CAT_STORE_NIB4 ? round_up((W + 1) / 2, 16)
+                                                                                           : round_up(W, 16);
+}
+
+// Packs uint8 rows into `storage` (BIT1 or NIB4) or unpacks them back.
+cudaError_t pack_rows(int32_t storage, const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
+                      int64_t W, cudaStream_t s) {
+  return storage == CAT_STORE_BIT1 ? cat::pack_bits_launch(src, spitch, dst, dpitch, rows, W, s)
+                                   : cat::pack_nib_launch(src, spitch, dst, dpitch, rows, W, s);
+}
+cudaError_t unpack_rows(int32_t storage, const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch,
+                        int64_t rows, int64_t W, cudaStream_t s) {
+  return storage == CAT_STORE_BIT1 ? cat::unpack_bits_launch(src, spitch, dst, dpitch, rows, W, s)
+                                   : cat::unpack_nib_launch(src, spitch, dst, dpitch, rows, W, s);
+}
+
+// Reallocates the state of h in `storage`, converting the current grid
+// (through a temporary uint8 copy when neither storage is uint8).
 int change_storage(cat_instance *h, int32_t storage) {
-  const int64_t pitch = storage == CAT_STORE_BIT1 ? round_up((h->W + 7) / 8, 16) : round_up(h->W, 16);
+  const int64_t pitch = storage_pitch(storage, h->W);
   const size_t bytes = (size_t)(pitch * h->H);
-  uint8_t *nb[2] = {nullptr, nullptr};
+  uint8_t *nb[2] = {nullptr, nullptr}, *tmp = nullptr;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMalloc(&nb[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&nb[1], bytes);
   if (e == cudaSuccess) e = cudaMemset(nb[0], 0, bytes);
   if (e == cudaSuccess) e = cudaMemset(nb[1], 0, bytes);
-  if (e == cudaSuccess)
-    e = storage == CAT_STORE_BIT1 ? cat::pack_bits_launch(h->origin(h->cur), h->pitch, nb[0], pitch, h->H, h->W, 0)
-                                  : cat::unpack_bits_launch(h->origin(h->cur), h->pitch, nb[0], pitch, h->H, h->W, 0);
+  const uint8_t *u8 = h->origin(h->cur);   // the grid one byte per cell
+  int64_t u8_pitch = h->pitch;
+  if (e == cudaSuccess && h->storage != CAT_STORE_U8) {
+    if (storage == CAT_STORE_U8) {
+      e = unpack_rows(h->storage, h->origin(h->cur), h->pitch, nb[0], pitch, h->H, h->W, 0);
+    } else {
+      e = cudaMalloc(&tmp, (size_t)(h->H * h->W));
+      if (e == cudaSuccess) e = unpack_rows(h->storage, h->origin(h->cur), h->pitch, tmp, h->W, h->H, h->W, 0);
+      u8 = tmp;
+      u8_pitch = h->W;
+    }
+  }
+  if (e == cudaSuccess && storage != CAT_STORE_U8) e = pack_rows(storage, u8, u8_pitch, nb[0], pitch, h->H, h->W, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tmp);
   if (e != cudaSuccess) {
     cudaFree(nb[0]);
     cudaFree(nb[1]);
@@ -411,7 +491,7 @@ int change_storage(cat_instance *h, int32_t storage) {
   return build_maps(h);
 }
 
-// uint8 rows <-> one-bit storage through a temporary device buffer.
+// uint8 rows <-> packed storage through a temporary device buffer.
 int bits_set_state(cat_instance *h, const uint8_t *src, int64_t pitch, cudaStream_t s) {
   const int64_t R = chunk_rows(h->W);
   uint8_t *tmp = nullptr;
@@ -420,11 +500,11 @@ int bits_set_state(cat_instance *h, const uint8_t *src, int64_t pitch, cudaStrea
   for (int64_t y = 0; y < h->H && e == cudaSuccess; y += R) {
     const int64_t n = std::min(R, h->H - y);
     e = cudaMemcpy2DAsync(tmp, (size_t)h->W, src + y * pitch, (size_t)pitch, (size_t)h->W, (size_t)n, cudaMemcpyDefault, s);
-    if (e == cudaSuccess) e = cat::pack_bits_launch(tmp, h->W, h->buf[h->cur] + y * h->pitch, h->pitch, n, h->W, s);
+    if (e == cudaSuccess) e = pack_rows(h->storage, tmp, h->W, h->buf[h->cur] + y * h->pitch, h->pitch, n, h->W, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(tmp);
-  if (e != cudaSuccess) return cuda_fail(e, "cat_set_state (one-bit storage)");
+  if (e != cudaSuccess) return cuda_fail(e, "cat_set_state (packed storage)");
   return CAT_OK;
 }
 
@@ -435,13 +515,13 @@ int bits_get_state(cat_instance *h, uint8_t *dst, int64_t pitch, cudaStream_t s)
   cudaError_t e = cudaSuccess;
   for (int64_t y = 0; y < h->H && e == cudaSuccess; y += R) {
     const int64_t n = std::min(R, h->H - y);
-    e = cat::unpack_bits_launch(h->buf[h->cur] + y * h->pitch, h->pitch, tmp, h->W, n, h->W, s);
+    e = unpack_rows(h->storage, h->buf[h->cur] + y * h->pitch, h->pitch, tmp, h->W, n, h->W, s);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(dst + y * pitch, (size_t)pitch, tmp, (size_t)h->W, (size_t)h->W, (size_t)n, cudaMemcpyDefault, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(tmp);
-  if (e != cudaSuccess) return cuda_fail(e, "cat_get_state (one-bit storage)");
+  if (e != cudaSuccess) return cuda_fail(e, "cat_get_state (packed storage)");
   return CAT_OK;
 }
 
@@ -468,8 +548,12 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   if (rc) return rc;
   if (boundary != CAT_BOUNDARY_ZERO && boundary != CAT_BOUNDARY_PERIODIC)
     return fail(CAT_ERR_INVALID_ARG, "unknown boundary %d", boundary);
-  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
+  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1 && storage != CAT_STORE_NIB4)
+    return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (storage == CAT_STORE_BIT1 && rule->C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
+  if (storage == CAT_STORE_NIB4 && (rule->C > 16 || boundary != CAT_BOUNDARY_ZERO || rule->nbhd != 'M' || rule->r > 16))
+    return fail(CAT_ERR_UNSUPPORTED, "four-bit storage holds rules with C <= 16, r <= 16, the Moore "
+                                     "neighbourhood and the zero boundary");
   if (storage == CAT_STORE_BIT1 && boundary != CAT_BOUNDARY_ZERO)
     return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
   if (storage == CAT_STORE_BIT1 && rule->nbhd != 'M')
@@ -484,16 +568,16 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   h->boundary = boundary;
   h->ghost = boundary == CAT_BOUNDARY_PERIODIC ? 16 : 0;
   h->storage = storage;
-  h->pitch = storage == CAT_STORE_BIT1 ? round_up((W + 7) / 8, 16) : round_up(W + 2 * h->ghost, 16);
+  h->pitch = storage == CAT_STORE_U8 ? round_up(W + 2 * h->ghost, 16) : storage_pitch(storage, W);
   h->rule = *rule;
   h->rd = reduce_rule(*rule);
   if (rule->nbhd == 'N' && (rule->C > 2 || rule->r > 16)) {  // the cross with C > 2 or r > 16: CUDA-core stencil
     h->kernel = CAT_KERNEL_STENCIL;
     h->dtype = CAT_DTYPE_INT8;
-  } else if (rule->r > 16) {  // beyond the tcgen05 window: the paper's fragment scheme with two halo fragments
+  } else if (rule->r > 16 && rule->C > 2) {  // the paper's fragment scheme with two halo fragments
     h->kernel = CAT_KERNEL_MMA_SYNC;
     h->dtype = CAT_DTYPE_FP16;
-  }
+  }   // r > 16 with C = 2: the tcgen05 wide tile
   const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
   cudaError_t e = cudaMalloc(&h->buf[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
@@ -515,23 +599,58 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
 
 int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage, int32_t steps_per_launch) {
   if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
-  if (kernel < CAT_KERNEL_AUTO || kernel > CAT_KERNEL_STENCIL) return fail(CAT_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  if (kernel < CAT_KERNEL_AUTO || kernel > CAT_KERNEL_RUNSUM) return fail(CAT_ERR_INVALID_ARG, "unknown kernel %d", kernel);
   if (dtype < CAT_DTYPE_AUTO || dtype > CAT_DTYPE_FP4_E2M1) return fail(CAT_ERR_INVALID_ARG, "unknown dtype %d", dtype);
-  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1) return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
+  if (storage != CAT_STORE_U8 && storage != CAT_STORE_BIT1 && storage != CAT_STORE_NIB4)
+    return fail(CAT_ERR_INVALID_ARG, "unknown storage %d", storage);
   if (steps_per_launch < 1) return fail(CAT_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
   const bool vn = h->rule.nbhd == 'N';
   const bool wide = h->rule.r > 16;
+  // AUTO: the autotuner's cached choice when CAT_AUTOTUNE_CACHE names a file
+  // holding one for this instance (with the storage asked for), else a fixed rule
+  int32_t tuned_tile = -1, tuned_window = 0;
+  if (kernel == CAT_KERNEL_AUTO && storage == h->storage) {
+    cat::InstanceInfo f{};
+    cat::host_instance_info(h, &f);
+    int32_t k = 0, d = 0, t = 0, w = 0, spl = 0;
+    if (cat::tune_cache_lookup_env(f, &k, &d, &t, &w, &spl) && k >= CAT_KERNEL_TCGEN05 && k <= CAT_KERNEL_BITSLICE &&
+        d >= CAT_DTYPE_AUTO && d <= CAT_DTYPE_FP4_E2M1 && spl >= 1) {
+      kernel = k;
+      dtype = d;
+      steps_per_launch = spl;
+      tuned_tile = t;
+      tuned_window = w;
+    }
+  }
   if (kernel == CAT_KERNEL_AUTO)
-    kernel = vn && (h->rule.C > 2 || wide) ? CAT_KERNEL_STENCIL : wide ? CAT_KERNEL_MMA_SYNC : CAT_KERNEL_TCGEN05;
+    kernel = vn && (h->rule.C > 2 || wide) ? CAT_KERNEL_STENCIL
+           : wide && h->rule.C > 2         ? CAT_KERNEL_MMA_SYNC
+                                           : CAT_KERNEL_TCGEN05;
+  const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
   if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
     return fail(CAT_ERR_UNSUPPORTED, dtype == CAT_DTYPE_INT8 ? "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC"
                                                              : "dtype %d is not served by the tcgen05 kernel", dtype);
   if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves FP16 and INT8 operands");
-  if (kernel == CAT_KERNEL_STENCIL) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
-  if (wide && (kernel == CAT_KERNEL_TCGEN05 || (kernel == CAT_KERNEL_MMA_SYNC && (dtype != CAT_DTYPE_FP16 || vn))))
-    return fail(CAT_ERR_UNSUPPORTED, "radii above 16 are served by the FP16 fragment kernel (Moore) and the stencil");
+  if (kernel == CAT_KERNEL_STENCIL || kernel == CAT_KERNEL_RUNSUM) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
+  if (kernel == CAT_KERNEL_RUNSUM && vn)
+    return fail(CAT_ERR_UNSUPPORTED, "the running-sum kernel serves the Moore neighbourhood");
+  if (kernel == CAT_KERNEL_BITSLICE) {   // bitwise adders on CUDA cores: no operand dtype
+    if (storage != CAT_STORE_BIT1 || h->rule.C != 2 || vn || h->ghost || h->rule.r > 3)
+      return fail(CAT_ERR_UNSUPPORTED, "the bit-sliced kernel serves one-bit storage, two-state Moore rules, "
+                                       "the zero boundary and r <= 3");
+    dtype = CAT_DTYPE_AUTO;
+  }
+  // the 96 x 96 tile: radii above 16 on tcgen05, or any radius after cat_set_tile(96, 96)
+  const bool wide_tc = kernel == CAT_KERNEL_TCGEN05 && !vn && (wide || cur_tile == 96);
+  if (wide_tc && (dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2 || storage != CAT_STORE_U8 || steps_per_launch > 1))
+    return fail(CAT_ERR_UNSUPPORTED,
+                "the 96 x 96 tcgen05 tile (r > 16) serves FP8 operands, two-state rules, uint8 storage, one step per launch");
+  if (wide && kernel == CAT_KERNEL_TCGEN05 && vn)
+    return fail(CAT_ERR_UNSUPPORTED, "the simplified von Neumann cross with r > 16 is served by the stencil");
+  if (wide && kernel == CAT_KERNEL_MMA_SYNC && (dtype != CAT_DTYPE_FP16 || vn))
+    return fail(CAT_ERR_UNSUPPORTED, "radii above 16 on MMA_SYNC are served with FP16 operands (Moore)");
   if (h->ghost && kernel != CAT_KERNEL_TCGEN05)
     return fail(CAT_ERR_UNSUPPORTED, "the periodic boundary is served by the tcgen05 kernel only");
   if (vn) {
@@ -545,8 +664,17 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (storage == CAT_STORE_BIT1) {
     if (h->rule.C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
-    if (kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3)
-      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 operands");
+    if ((kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3) && kernel != CAT_KERNEL_BITSLICE)
+      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 operands "
+                                       "and by the bit-sliced kernel");
+  }
+  if (storage == CAT_STORE_NIB4) {
+    if (h->rule.C > 16 || h->ghost || vn || wide)
+      return fail(CAT_ERR_UNSUPPORTED, "four-bit storage holds rules with C <= 16, r <= 16, the Moore "
+                                       "neighbourhood and the zero boundary");
+    if (kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3 || steps_per_launch > 1)
+      return fail(CAT_ERR_UNSUPPORTED, "four-bit storage is served by the tcgen05 kernel with FP8 operands, "
+                                       "one step per launch");
   }
   if (steps_per_launch > 1 && (kernel != CAT_KERNEL_TCGEN05 || vn || h->ghost))
     return fail(CAT_ERR_UNSUPPORTED, "several steps per launch are served by the tcgen05 Moore kernel with the zero boundary");
@@ -559,6 +687,46 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   h->kernel = kernel;
   h->dtype = dtype;
   h->steps_per_launch = steps_per_launch;
+  if (tuned_tile >= 0) {
+    h->tile = 0;
+    h->window = 0;
+    cat_set_tile(h, tuned_tile, tuned_tile, tuned_window);   // a stale entry keeps the radius's own tile
+  }
+  return CAT_OK;
+}
+
+int cat_get_options(cat_handle_t h, int32_t *kernel, int32_t *dtype, int32_t *storage, int32_t *steps_per_launch,
+                    int32_t *tile, int32_t *window_rows) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  if (kernel) *kernel = h->kernel;
+  if (dtype) *dtype = h->dtype;
+  if (storage) *storage = h->storage;
+  if (steps_per_launch) *steps_per_launch = h->steps_per_launch;
+  if (tile) *tile = h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' ? (wide_tile(h) ? 96 : 128) : 0;
+  if (window_rows) *window_rows = h->kernel != CAT_KERNEL_TCGEN05 || h->rule.nbhd != 'M' || wide_tile(h) ? 0
+                                  : short_window(h) ? 144 : 160;
+  return CAT_OK;
+}
+
+int cat_set_tile(cat_handle_t h, int32_t ty, int32_t tx, int32_t window_rows) {
+  if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
+  const bool t0 = ty == 0 && tx == 0, t128 = ty == 128 && tx == 128, t96 = ty == 96 && tx == 96;
+  if (!t0 && !t128 && !t96) return fail(CAT_ERR_INVALID_ARG, "tile %d x %d: choose 0 x 0, 128 x 128 or 96 x 96", ty, tx);
+  if (window_rows != 0 && window_rows != 144 && window_rows != 160)
+    return fail(CAT_ERR_INVALID_ARG, "window of %d rows: choose 0, 144 or 160", window_rows);
+  const bool vn = h->rule.nbhd == 'N';
+  if (t128 && h->rule.r > 16) return fail(CAT_ERR_UNSUPPORTED, "the 128 x 128 tile serves radii up to 16");
+  if (t96 && (h->kernel != CAT_KERNEL_TCGEN05 || vn || h->dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2 ||
+              h->storage != CAT_STORE_U8 || h->ghost || h->steps_per_launch > 1))
+    return fail(CAT_ERR_UNSUPPORTED, "the 96 x 96 tile serves the tcgen05 Moore kernel with FP8 operands, two-state "
+                                     "rules, uint8 storage, the zero boundary and one step per launch");
+  if (window_rows == 144 && (t96 || h->rule.r > 7 || h->kernel != CAT_KERNEL_TCGEN05 || vn ||
+                             h->dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2 || h->storage != CAT_STORE_U8))
+    return fail(CAT_ERR_UNSUPPORTED, "the 144-row window serves the 128 x 128 tcgen05 Moore kernel with FP8 "
+                                     "operands, two-state rules, uint8 storage and r <= 7");
+  if (h->tile != (t0 ? 0 : ty) || h->window != window_rows) drop_plans_with(h);
+  h->tile = t0 ? 0 : ty;
+  h->window = window_rows;
   return CAT_OK;
 }
 
@@ -575,7 +743,7 @@ int cat_set_state(cat_handle_t h, const uint8_t *src, int64_t pitch, int32_t src
   (void)src_on_device;  // unified addressing tells host and device memory apart
   if (!h || !src) return fail(CAT_ERR_INVALID_ARG, "NULL handle or source");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
-  if (h->storage == CAT_STORE_BIT1) return bits_set_state(h, src, pitch, (cudaStream_t)stream);
+  if (h->storage != CAT_STORE_U8) return bits_set_state(h, src, pitch, (cudaStream_t)stream);
   return copy2d(h->origin(h->cur), h->pitch, src, pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
@@ -583,7 +751,7 @@ int cat_get_state(cat_handle_t h, uint8_t *dst, int64_t pitch, int32_t dst_on_de
   (void)dst_on_device;
   if (!h || !dst) return fail(CAT_ERR_INVALID_ARG, "NULL handle or destination");
   if (pitch < h->W) return fail(CAT_ERR_INVALID_ARG, "pitch %lld < W %lld", (long long)pitch, (long long)h->W);
-  if (h->storage == CAT_STORE_BIT1) return bits_get_state(h, dst, pitch, (cudaStream_t)stream);
+  if (h->storage != CAT_STORE_U8) return bits_get_state(h, dst, pitch, (cudaStream_t)stream);
   return copy2d(dst, pitch, h->origin(h->cur), h->pitch, h->W, h->H, (cudaStream_t)stream);
 }
 
@@ -619,7 +787,7 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   bool all_tc = true;   // Moore, zero boundary, uint8 storage: other instances step one by one
   for (int32_t i = 0; i < count; ++i) {
     all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8 &&
-              hs[i]->rule.nbhd == 'M' && hs[i]->rule.r <= 16;
+              hs[i]->rule.nbhd == 'M' && !wide_tile(hs[i]);
     if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
       return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
     if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)

@@ -91,8 +91,29 @@ enum : int32_t { kDevErrTimeout = 0x100 };
 cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits, int grid, cudaStream_t s);
 // Simplified von Neumann neighbourhood (FP8, C = 2, single instance).
 cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s);
+// The 96 x 96 tile with a 32-cell halo, radii up to 32 (FP8, C = 2, single
+// instance): map_in_a / map_in_b the 128 x 160 and 32 x 160 window maps,
+// map_ctr / map_out the 96 x 96 tile maps; tiles_x, n_tiles in 96 x 96 tiles.
+cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s);
+// Four bits per cell (FP8 on a re-encoded window, C <= 16, single instance):
+// map_in_a the 96 x 160-byte window map, map_ctr / map_out the 64 x 128-byte
+// tile maps (64B swizzle) of the packed buffers.
+cudaError_t nib_launch(const TcParams &p, int grid, cudaStream_t s);
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s);
 size_t tc_smem_bytes(int dt, bool encode, bool sw);
+
+// What the autotuner needs to know about an instance (cat_api.cu).
+struct InstanceInfo {
+  int64_t H, W;
+  cat_rule_t rule;
+  int32_t boundary, storage, kernel, dtype, tile, window, steps_per_launch;
+};
+int host_instance_info(cat_handle_t h, InstanceInfo *out);
+// The autotuner's cached choice for an instance from the JSON-lines file named
+// by the environment variable CAT_AUTOTUNE_CACHE (cat_tune.cu); false when
+// the variable is unset or the file holds no entry for the instance.
+bool tune_cache_lookup_env(const InstanceInfo &info, int32_t *kernel, int32_t *dtype, int32_t *tile,
+                           int32_t *window, int32_t *spl);
 
 // Host helpers defined in cat_api.cu (error message of the calling thread,
 // rule checks, TMA descriptor encoding of a uint8 grid).
@@ -109,6 +130,13 @@ cudaError_t pack_bits_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, i
                              int64_t W, cudaStream_t s);
 cudaError_t unpack_bits_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
                                int64_t W, cudaStream_t s);
+// Four bits per cell (cat_bits.cu): rows of W cells <-> rows of (W + 1) / 2
+// bytes, cell x in nibble x % 2 of byte x / 2 (states 0..15; the nibble past
+// an odd W is 0).
+cudaError_t pack_nib_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
+                            int64_t W, cudaStream_t s);
+cudaError_t unpack_nib_launch(const uint8_t *src, int64_t spitch, uint8_t *dst, int64_t dpitch, int64_t rows,
+                              int64_t W, cudaStream_t s);
 
 // Periodic boundary (cat_halo.cu): fills the G-cell ghost frame around the
 // H x W grid whose cell (0, 0) is at base + G * pitch + G with the cells the
@@ -117,7 +145,13 @@ cudaError_t ghost_fill_launch(uint8_t *base, int64_t pitch, int64_t H, int64_t W
 
 // Paper-style fragment kernels (cat_mma.cu).  dt: FP16 or INT8.
 cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s);
-// Shared-memory CUDA-core stencil (cat_stencil.cu).
+// Shared-memory CUDA-core stencil, and the separable running-sum kernel
+// (cat_stencil.cu).
 cudaError_t stencil_launch(const SimpleParams &p, cudaStream_t s);
+cudaError_t runsum_launch(const SimpleParams &p, cudaStream_t s);
+// Bit-sliced CUDA-core step on one-bit storage, r <= 3 (cat_swar.cu): in/out
+// are packed rows at `pitch` bytes (a multiple of 4); sums: counts instead.
+cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
+                        int32_t *sums, int64_t sums_ld, cudaStream_t s);
 
 }  // namespace cat

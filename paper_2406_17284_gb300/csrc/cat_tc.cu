@@ -32,7 +32,8 @@
 //                (0x01 reads as e4m3 2^-9), so D1 = H * 2^-9 exactly; pass 2
 //                takes H * 2^-9 as e4m3 when 2r+1 <= 15 (all such values are
 //                e4m3 numbers) and as f16 otherwise (e4m3 cannot hold the odd
-//                counts above 16); D2 = S * 2^-9.
+//                counts above 16); D2 = S * 2^-9.  The wide tile (r <= 32,
+//                H <= 65) splits H into e4m3 digits instead (see Tm).
 // The epilogue compares S (as f16, exact up to 2048) against the rule's
 // ranges two cells at a time in half2 arithmetic.
 //
@@ -41,8 +42,8 @@
 // pass-2 MMA issuer, warps 4..11 = convert warps (D1 -> pass-2 operand,
 // window encoding when needed, bands), warps 12..27 = epilogue warps (fused
 // transition).  The two worker roles
-// work on different tiles at once; tensor memory holds two accumulator
-// regions (D1, then D2, of one tile each) and the bands.  Both products
+// work on different tiles at once; tensor memory holds the accumulator
+// regions and the bands (see Tm below).  Both products
 // accumulate in f16 (exact: every partial sum is a multiple of the operand
 // scale no larger than 1089 times it), so the workers read f16 pairs straight
 // from TMEM.  Every wait is bounded; on timeout the CTA records
@@ -75,10 +76,17 @@ constexpr int kMaxRegions = 3;
 // two e4m3 bands -- pass 1's (window columns offset by 16) and pass 2's
 // (window rows offset by 8): 3 * 144 + 40 + 40 = 512.  Three tiles are then in
 // flight instead of two.
-template <bool SW>
+// Wide tile (WIDE, radii up to 32): a 96 x 96 output tile inside the same
+// 160 x 160 window, which then starts 32 cells above and left of the tile
+// (96 + 2 * 32 = 160; x0 - 32 stays 16-byte aligned since x0 is a multiple of
+// 96).  The bands have offset 32 and rows 96..127 zero, so the MMA shapes stay
+// M = 128, K = 160; pass 2 has N = 96.
+template <bool SW, bool WIDE = false>
 struct Geo {
+  static constexpr int kTS = WIDE ? 96 : 128;         // output tile side
+  static constexpr int kXOff = WIDE ? 32 : 16;        // window columns left of the tile
   static constexpr int kRows = SW ? 144 : 160;        // window rows = pass-1 N
-  static constexpr int kYOff = SW ? 8 : 16;           // window rows above the tile
+  static constexpr int kYOff = WIDE ? 32 : (SW ? 8 : 16);   // window rows above the tile
   static constexpr int kRegions = SW ? 3 : 2;
   static constexpr int kRegionCols = SW ? 144 : 160;
   static constexpr uint32_t kBand16 = 320;            // f16 band (standard only)
@@ -86,6 +94,36 @@ struct Geo {
   static constexpr uint32_t kBand8P2 = SW ? 472 : 416;  // e4m3 band for pass 2 (offset kYOff)
 };
 constexpr uint32_t kTmemCols = 512;
+
+// Tensor-memory map of a kernel.  In the 128 x 128 kernels a tile's D2
+// overwrites its D1 region, which stays taken from pass 1 until the epilogue
+// has read S: two 160-column regions beside the f16 band (80 columns, pass 2
+// when 2r+1 > 15, and the FP16 kernel) and the e4m3 band (40), or three
+// 144-column regions in the short window.  The wide tile (DEC) keeps them
+// apart: two 160-column D1 regions, free again once the convert warps have
+// read H, and one 96-column D2 region, free once the epilogue has read S.
+// Its counts reach 4225, so D2 accumulates in f32 and H (up to 65) splits into
+// H & 15 and H >> 4 (at most 4), both e4m3 codes of themselves times 2^-9,
+// the second against a band of 16s: 2 * 160 + 96 + 40 + 40 = 496 columns.
+// (The same split for the 128 x 128 FP8 kernel -- pass 2 on e4m3 for every r,
+// no f16 band, and separate D1 / D2 regions, 2 + 1 or 1 + 2 -- measured 8%
+// and 3% slower at r >= 8 than the shared regions, 2.05 and 2.15 against
+// 2.22 * 10^12 cell updates/s, so it is not used there.)
+template <int DT, bool SW, bool WIDE = false>
+struct Tm {
+  static constexpr bool kDec = DT == 1 && !SW && WIDE;
+  static constexpr int kND1 = kDec ? 2 : Geo<SW>::kRegions;
+  static constexpr int kND2 = kDec ? 1 : Geo<SW>::kRegions;
+  static constexpr uint32_t kD1Cols = Geo<SW>::kRegionCols;
+  static constexpr uint32_t kD2Base = kDec ? kND1 * kD1Cols : 0;
+  static constexpr uint32_t kD2Cols = kDec ? Geo<SW, WIDE>::kTS : Geo<SW>::kRegionCols;
+  static constexpr uint32_t kBand16 = Geo<SW>::kBand16;     // FP16 kernel only
+  static constexpr uint32_t kBand8 = kDec ? kD2Base + kND2 * kD2Cols : Geo<SW>::kBand8;
+  static constexpr uint32_t kBand8P2 = kDec ? kBand8 : Geo<SW>::kBand8P2;
+  static constexpr uint32_t kBand8x16 = kBand8 + 40;        // wide tile: the band of 16s
+  static_assert(!kDec || kBand8 + (WIDE ? 80 : 40) <= kTmemCols, "tensor memory budget");
+  static_assert(kND1 <= kMaxRegions && kND2 <= kMaxRegions, "barrier arrays");
+};
 
 // Byte offset of the element at byte position kb (= k * E) of row `row` in a
 // K-major operand tile of R rows.  A row holds 160 elements of E bytes, split
@@ -128,12 +166,13 @@ __device__ __forceinline__ uint64_t op_desc_k(const OpDesc &d) {
 // Issues the K-steps of one band product: D = A[M=128, K=160] x B[N, K=160]^T
 // with the band A in tensor memory (32 bytes of K = 8 columns per step) and
 // B in shared memory.
-template <int KIND, int RB, int E, int J = 0>
+// ACC: the first K-step adds to D instead of overwriting it.
+template <int KIND, int RB, int E, bool ACC = false, int J = 0>
 __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDesc &b, uint32_t idesc) {
   if constexpr (J < 5 * E) {
-    if constexpr (KIND == 0) mma_f16_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, J > 0);
-    else mma_f8f6f4_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, J > 0);
-    band_mma<KIND, RB, E, J + 1>(d, a_tmem, b, idesc);
+    if constexpr (KIND == 0) mma_f16_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, ACC || J > 0);
+    else mma_f8f6f4_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, ACC || J > 0);
+    band_mma<KIND, RB, E, ACC, J + 1>(d, a_tmem, b, idesc);
   }
 }
 
@@ -147,15 +186,19 @@ __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDe
 // lowest bit); a window stage is then one 48-byte x 160-row box (cells x0 - 128
 // .. x0 + 255, of which the window uses x0 - 16 .. x0 + 143) that the convert
 // warps unpack into the e4m3 operand, and a ring entry is 16 bytes x 128 rows.
-template <int DT, bool ENC, bool SW = false, bool BITS = false>
+// NIB: four bits per cell (two cells per byte, the even x in the low nibble);
+// a window stage is one 96-byte x 160-row box (cells x0 - 32 .. x0 + 159),
+// unpacked by the convert warps into the e4m3 operand, and a ring entry is 64
+// bytes x 128 rows (64B swizzle).
+template <int DT, bool ENC, bool SW = false, bool BITS = false, bool WIDE = false, bool NIB = false>
 struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
-  static constexpr int NS = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
-  static constexpr int NR = (SW || BITS) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
+  static constexpr int NS = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
+  static constexpr int NR = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
   static constexpr int NE = BITS ? 3 : ((DT == 1 && ENC) ? 2 : 1);  // encoded windows (FP8: encode ahead)
   static constexpr int NH = SW ? 3 : 2;                       // pass-2 operand buffers
   static constexpr uint32_t kXs = 0;                          // raw windows (TMA)
-  static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : kWin * Geo<SW>::kRows;  // bytes one window load delivers
+  static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : NIB ? 96 * kWin : kWin * Geo<SW>::kRows;  // one window load
   static constexpr uint32_t kXsStride = (kXsBytes + 1023) / 1024 * 1024;  // 128B-swizzle atoms stay aligned
   static constexpr uint32_t kXe = kXs + NS * kXsStride;       // encoded window
   static constexpr uint32_t kXeStride = kWin * kWin * E1;     // one encoded window (25 or 50 KiB)
@@ -163,7 +206,7 @@ struct Layout {
   static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand (K padded to 160)
   static constexpr uint32_t kHBytes = kTile * kWin * (SW ? 1 : 2);
   static constexpr uint32_t kRing = kH + NH * kHBytes;        // centre tiles / output staging
-  static constexpr uint32_t kRingBytes = BITS ? 16 * kTile : kTile * kTile;
+  static constexpr uint32_t kRingBytes = BITS ? 16 * kTile : NIB ? 64 * kTile : Geo<SW, WIDE>::kTS * Geo<SW, WIDE>::kTS;
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
   static_assert(kDyn <= 232448, "shared memory budget");
@@ -178,6 +221,7 @@ struct Bars {
   uint64_t c_full[kMaxStages], out_full[kMaxStages];
   uint64_t d1_full[kMaxRegions], d2_full[kMaxRegions], tmem_empty[kMaxRegions];
   uint64_t h_full[3], enc_full[3], band_ready;
+  uint64_t d1_empty[kMaxRegions], h_empty[3];   // wide tile: D1 read, H read
   uint64_t mma_done[2], never;
   uint32_t tmem_base;
   int abort;
@@ -253,6 +297,40 @@ __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, in
   }
 }
 
+// Bytes 0/1 of four nibble flags 0/1 held in the 16-bit field `sel` (0x4140:
+// the low half of a, 0x4342: the high half) of a.
+__device__ __forceinline__ uint32_t nib4_to_bytes(uint32_t a, uint32_t sel) {
+  const uint32_t t = __byte_perm(a, 0, sel);   // the field's two bytes in bytes 0 and 2
+  return (t | (t << 4)) & 0x0F0F0F0Fu;
+}
+
+// Unpacks a four-bit window stage (160 rows of 96 bytes, window cell x' in
+// nibble x' % 2 of byte 8 + x' / 2) into the e4m3 window operand: 0x01 for
+// state 1, else 0.  Item = one 16-cell chunk of a row (eight source bytes);
+// consecutive threads take consecutive chunks of a row.
+__device__ __forceinline__ void unpack_nib_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
+  for (int q = tid; q < kWin * 10; q += nthr) {
+    const int row = q / 10, c = q - row * 10;
+    const uint2 v = *reinterpret_cast<const uint2 *>(xs + row * 96 + 8 + 8 * c);
+    uint32_t f[2];
+    const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {   // nibble 1 where the state is 1 (borrow-free nibble test)
+      const uint32_t x = w[i] ^ 0x11111111u;
+      const uint32_t nz = (((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u;
+      f[i] = (nz ^ 0x88888888u) >> 3;
+    }
+    *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
+        make_uint4(nib4_to_bytes(f[0], 0x4140), nib4_to_bytes(f[0], 0x4342), nib4_to_bytes(f[1], 0x4140),
+                   nib4_to_bytes(f[1], 0x4342));
+  }
+}
+
+// Packs the states of four cells (bytes 0..3 of w, each below 16) pairwise:
+// byte 0 of the result holds cells 0 and 1 (low and high nibble), byte 2
+// cells 2 and 3; bytes 1 and 3 hold no cell.
+__device__ __forceinline__ uint32_t bytes_to_nib_pairs(uint32_t w) { return w | (w >> 4); }
+
 // Band B[m][k] = one iff k - m in [off - r, off + r] as an A operand in tensor
 // memory: row m in lane m, K packed along the columns (two f16 values, or four
 // e4m3 values, per column, the lowest k in the low bits); 80 columns (f16) or
@@ -261,19 +339,26 @@ __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, in
 // short-window kernels hold two e4m3 bands, offset 16 (pass 1) and offset 8
 // (pass 2).  Convert warp (q, kq) writes lanes 32q .. 32q+31 and every other
 // 8-column chunk from chunk kq.
-template <int DT, bool SW>
+template <int DT, bool SW, bool WIDE = false>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
-  using G = Geo<SW>;
-  // chunks [0, n0) belong to the first band, [n0, n) to the second
-  constexpr int n0 = SW ? 5 : 10, n = SW ? 10 : (DT == 1 ? 15 : 10);
+  using G = Geo<SW, WIDE>;
+  using T = Tm<DT, SW, WIDE>;
+  // chunks [0, n0) belong to the first band, [n0, n) to the second: the f16
+  // band (standard window; the FP16 kernel has only this one) and the e4m3
+  // band, or in the short window the e4m3 bands of pass 1 and pass 2, or in
+  // the wide tile the e4m3 band and the band of 16s (offset 32, rows 96..127
+  // zero)
+  constexpr int n0 = WIDE ? 5 : (SW ? 5 : 10), n = WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
   for (int c = kq; c < n; c += 2) {                 // warp-uniform
     const bool first = c < n0;
-    const bool f16 = !SW && first;
+    const bool f16 = !SW && !WIDE && first;
     const int cc = first ? c : c - n0;
-    const int off = (SW && !first) ? G::kYOff : 16;
-    const uint32_t col = SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : G::kBand8);
+    const int off = WIDE ? G::kXOff : (SW && !first) ? G::kYOff : 16;
+    const uint32_t col = WIDE ? (first ? T::kBand8 : T::kBand8x16)
+                       : SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : T::kBand8);
+    const uint32_t one8 = (WIDE && !first) ? 0x58u : 0x38u;   // e4m3 16.0 or 1.0
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -285,11 +370,11 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
           const int d = k0 + b - m;
           if (d >= off - r && d <= off + r) w |= 0x3C00u << (16 * b);
         }
-      } else {
+      } else if (m < G::kTS) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int d = k0 + b - m;
-          if (d >= off - r && d <= off + r) w |= 0x38u << (8 * b);
+          if (d >= off - r && d <= off + r) w |= one8 << (8 * b);
         }
       }
       v[i] = w;
@@ -397,6 +482,41 @@ __device__ __forceinline__ uint32_t rule4_multistate_h(uint32_t s01, uint32_t s2
   return (inr & dead) | ((0x02020202u - inr) & (alive * 0xFFu)) | (aged & (dying * 0xFFu));
 }
 
+// The rule's two ranges scaled like a wide tile's f32 accumulator (S * scale,
+// counts up to 4225).  An empty range gets lo above hi, both above any count.
+struct FloatRule {
+  float bl, bh, sl, sh;
+};
+
+__device__ __forceinline__ FloatRule make_float_rule(const RuleDev &R, float scale) {
+  auto lo_of = [](int lo) { return lo > 4225 ? 65536.0f : (float)lo; };
+  auto hi_of = [](int lo, int w) { return lo > 4225 ? 32768.0f : fminf((float)lo + (float)w, 65536.0f); };
+  return FloatRule{lo_of(R.b_lo) * scale, hi_of(R.b_lo, R.b_w) * scale, lo_of(R.s_lo) * scale,
+                   hi_of(R.s_lo, R.s_w) * scale};
+}
+
+// 0xFF in byte k where float k is negative (its sign byte replicated by prmt).
+__device__ __forceinline__ uint32_t sign_bytes4(float a, float b, float c, float d) {
+  uint32_t lo, hi;
+  asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(lo) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
+  asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(hi) : "r"(__float_as_uint(c)), "r"(__float_as_uint(d)));
+  return __byte_perm(lo, hi, 0x5410);
+}
+
+// Next states of four cells of a two-state rule from their counts as f32
+// (S * scale) and their current states (bytes 0/1 of cw): both range tests
+// (s - lo)(hi - s) >= 0 per cell, as in rule4_binary_h (every nonzero factor
+// is a multiple of the scale, so no product underflows to zero), and the
+// centre picks survival or birth.
+__device__ __forceinline__ uint32_t rule4_binary_f(const float *s, uint32_t cw, const FloatRule &f) {
+  const uint32_t out_s = sign_bytes4((s[0] - f.sl) * (f.sh - s[0]), (s[1] - f.sl) * (f.sh - s[1]),
+                                     (s[2] - f.sl) * (f.sh - s[2]), (s[3] - f.sl) * (f.sh - s[3]));
+  const uint32_t out_b = sign_bytes4((s[0] - f.bl) * (f.bh - s[0]), (s[1] - f.bl) * (f.bh - s[1]),
+                                     (s[2] - f.bl) * (f.bh - s[2]), (s[3] - f.bl) * (f.bh - s[3]));
+  const uint32_t alive = cw * 0xFFu;
+  return ~((out_s & alive) | (out_b & ~alive)) & 0x01010101u;
+}
+
 __device__ __forceinline__ float half_lo(uint32_t h2) { return __low2float(as_h2(h2)); }
 __device__ __forceinline__ float half_hi(uint32_t h2) { return __high2float(as_h2(h2)); }
 
@@ -429,7 +549,7 @@ __device__ __forceinline__ void my_range(const TcParams &p, int &first, int &cou
 // by a fixed step without a division.  MS: a single instance stepped several
 // times in one launch walks its `per` tiles once per step; odd steps use the
 // second set of maps.
-template <bool BATCH, bool MS = false>
+template <bool BATCH, bool MS = false, int TS = kTile>
 struct TileSeq {
   int first, j, tx, ty, sx, sy;
   int k, per, step;   // single instance: tile k of this CTA's `per` tiles in step `step`
@@ -483,8 +603,8 @@ struct TileSeq {
       t.in_b = odd ? &p.map2_in_b : &p.map_in_b;
       t.out = odd ? &p.map2_out : &p.map_out;
       t.ctr = odd ? &p.map2_ctr : &p.map_ctr;
-      t.x0 = tx * kTile;
-      t.y0 = ty * kTile;
+      t.x0 = tx * TS;
+      t.y0 = ty * TS;
       t.tx0 = t.x0 + p.ox;
       t.ty0 = t.y0 + p.oy;
       t.H = p.H;
@@ -513,16 +633,23 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 // exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
-template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS>
+template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS, bool WIDE = false, bool NIB = false>
 __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   static_assert(!MS || !BATCH, "several steps per launch serve single instances");
+  static_assert(!WIDE || (DT == 1 && !ENC && !BATCH && !SW && !BITS && !MS),
+                "the wide tile serves single two-state instances on FP8 operands, one step per launch");
   static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
+  static_assert(!NIB || (DT == 1 && ENC && !SW && !BITS && !WIDE && !BATCH && !MS),
+                "four-bit storage runs the FP8 kernel on a re-encoded window, single instance, one step per launch");
   static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
                 Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
-  using L = Layout<DT, ENC, SW, BITS>;
-  using G = Geo<SW>;
-  constexpr int kRegions = G::kRegions;
-  constexpr int kRegionCols = G::kRegionCols;
+  using L = Layout<DT, ENC, SW, BITS, WIDE, NIB>;
+  // x-coordinate of a tile's centre box in its tensor map (bytes of packed rows)
+  auto ctr_x = [](int tx0) { return BITS ? tx0 / 8 : NIB ? tx0 / 2 : tx0; };
+  using G = Geo<SW, WIDE>;
+  using T = Tm<DT, SW, WIDE>;
+  constexpr bool DEC = T::kDec;       // D1 and D2 in separate regions, pass 2 on e4m3 digits
+  constexpr int ND1 = T::kND1, ND2 = T::kND2;
   constexpr int E1 = L::E1;
   constexpr int NS = L::NS;
   constexpr int NR = L::NR;
@@ -551,12 +678,16 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       mbar_init(&bars->c_full[i], 1);
       mbar_init(&bars->out_full[i], kEpiWarps);
     }
-    for (int i = 0; i < kRegions; ++i) {
+    for (int i = 0; i < kMaxRegions; ++i) {
       mbar_init(&bars->d1_full[i], 1);
+      mbar_init(&bars->d1_empty[i], kCvtWarps);
       mbar_init(&bars->d2_full[i], 1);
       mbar_init(&bars->tmem_empty[i], kEpiWarps);
     }
-    for (int i = 0; i < 3; ++i) mbar_init(&bars->h_full[i], kCvtWarps);
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(&bars->h_full[i], kCvtWarps);
+      mbar_init(&bars->h_empty[i], 1);
+    }
     for (int i = 0; i < L::NE; ++i) mbar_init(&bars->enc_full[i], kCvtWarps);
     mbar_init(&bars->band_ready, kCvtWarps);
     mbar_init(&bars->mma_done[0], 1);
@@ -588,6 +719,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
     uint8_t *xe = smem + L::kXe + e * L::kXeStride;
     if constexpr (BITS) unpack_window(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
+    else if constexpr (NIB) unpack_nib_window(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
     else encode_window<L::E1>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, tid, nthr);
     fence_proxy_async_smem();
     __syncwarp();
@@ -600,7 +732,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     // Streams the haloed windows into NS stages (freed by pass 1 or the encoder).
     if (lane == 0) {
       int issued = 0;
-      TileSeq<BATCH, MS> seq(p, first, n_my);
+      TileSeq<BATCH, MS, G::kTS> seq(p, first, n_my);
       for (int j = 0; j < n_all; ++j, seq.next(p)) {
         const int s = j % NS;
         const Tile t = seq.get(p);
@@ -619,9 +751,11 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         mbar_arrive_expect_tx(&bars->x_full[s], L::kXsBytes);
         if constexpr (BITS) {   // bytes x0/8 - 16 .. x0/8 + 31: 16-byte aligned
           tma_load_2d(xs, t.in_a, t.tx0 / 8 - 16, t.ty0 - 16, &bars->x_full[s]);
+        } else if constexpr (NIB) {   // bytes x0/2 - 16 .. x0/2 + 79: 16-byte aligned
+          tma_load_2d(xs, t.in_a, t.tx0 / 2 - 16, t.ty0 - 16, &bars->x_full[s]);
         } else {
-          tma_load_2d(xs, t.in_a, t.tx0 - 16, t.ty0 - G::kYOff, &bars->x_full[s]);
-          tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 + 112, t.ty0 - G::kYOff, &bars->x_full[s]);
+          tma_load_2d(xs, t.in_a, t.tx0 - G::kXOff, t.ty0 - G::kYOff, &bars->x_full[s]);
+          tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 - G::kXOff + 128, t.ty0 - G::kYOff, &bars->x_full[s]);
         }
         issued = j + 1;
       }
@@ -631,15 +765,17 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     }
   } else if (warp == 1) {
     // ---------------------------------------------------- pass-1 MMA issuer
-    // D1 of tile j into region j % 2 once the epilogue has read that region's
-    // previous D2, the window is in place and the bands match the radius.
+    // D1 of tile j into its region once that region is free (wide tile: the
+    // convert warps have read its previous D1; otherwise the epilogue has
+    // read its previous D2), the window is in place and the bands match the
+    // radius.
     // Each issuer blocks on exactly the barrier it needs next, so neither
     // polls; the two passes are issued from different warps.
     if (lane == 0) {
       // f16 accumulators: every partial sum is a multiple of the operand scale
       // up to 1089 * scale, which f16 represents exactly
       const uint32_t idesc1 = idesc_f16acc(128, G::kRows);
-      const uint32_t band1 = tmem + (DT == 1 ? G::kBand8 : G::kBand16);
+      const uint32_t band1 = tmem + (DT == 1 ? T::kBand8 : T::kBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -648,14 +784,16 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       }
       int band_r = -1, builds = 0;
       for (int j = 0; ok && j < n_all; ++j) {
-        const int reg = j % kRegions, s = j % NS;
+        const int reg = j % ND1, s = j % NS;
         const int r = tile_rule<BATCH>(p, first, j).r;
         if (r != band_r) {                 // the convert warps have built the bands for r
           if (!(ok = mbar_wait(&bars->band_ready, builds & 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 4); break; }
           ++builds;
           band_r = r;
         }
-        if (!(ok = mbar_wait(&bars->tmem_empty[reg], ((j / kRegions) & 1) ^ 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 5); break; }
+        // the region is free: its D1 converted (DEC), or its D2 read by the epilogue
+        uint64_t *free_bar = DEC ? &bars->d1_empty[reg] : &bars->tmem_empty[reg];
+        if (!(ok = mbar_wait(free_bar, ((j / ND1) & 1) ^ 1, &bars->abort, p.timeout_ns))) { set_abort(bars, err0, 5); break; }
         if (ENC) ok = mbar_wait(&bars->enc_full[j % L::NE], (j / L::NE) & 1, &bars->abort, p.timeout_ns);
         else ok = mbar_wait(&bars->x_full[s], (j / NS) & 1, &bars->abort, p.timeout_ns);
         if (!ok) { set_abort(bars, err0, 6); break; }
@@ -663,7 +801,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         const uint64_t soff = ENC ? (uint64_t)(((j % L::NE) * L::kXeStride) >> 4)   // encoded window
                                   : (uint64_t)((s * L::kXsStride) >> 4);             // window stage
         const OpDesc win{win0.d128 + soff, win0.d32 + soff};
-        band_mma<DT == 0 ? 0 : 1, G::kRows, E1>(tmem + reg * kRegionCols, band1, win, idesc1);
+        band_mma<DT == 0 ? 0 : 1, G::kRows, E1>(tmem + reg * T::kD1Cols, band1, win, idesc1);
         mma_commit(&bars->d1_full[reg]);
         if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
       }
@@ -682,7 +820,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       int issued = 0;
       if constexpr (MS) {
         int passed = 0;       // centre tiles loaded; steps whose loads may start
-        TileSeq<BATCH, true> lseq(p, first, n_my), sseq(p, first, n_my);
+        TileSeq<BATCH, true, G::kTS> lseq(p, first, n_my), sseq(p, first, n_my);
         // loads the centre tiles up to (not including) tile `limit` whose step
         // has passed its grid barrier, each into the entry its tile - NR freed
         auto load_ctr = [&](int limit) {
@@ -691,7 +829,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
             const Tile t = lseq.get(p);
             if (lseq.k == 0 || BATCH) prefetch_tmap(t.ctr);
             mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-            tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
+            tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, ctr_x(t.tx0), t.ty0, &bars->c_full[k]);
             lseq.next(p);
             ++issued;
           }
@@ -702,7 +840,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           const Tile t = sseq.get(p);
           if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
           if (BATCH || !p.sums) {
-            tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
+            tma_store_2d(t.out, ctr_x(t.tx0), t.ty0, smem + L::kRing + k * L::kRingBytes);
             bulk_commit();
             bulk_wait_read<0>();          // the store has read the entry
           }
@@ -722,13 +860,13 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           load_ctr(j + 1 + NR);
         }
       } else {
-        TileSeq<BATCH> lseq(p, first), sseq(p, first);
+        TileSeq<BATCH, false, G::kTS> lseq(p, first), sseq(p, first);
         auto load_ctr = [&](int j) {
           const int k = j % NR;
           const Tile t = lseq.get(p);
           if (j == 0 || BATCH) prefetch_tmap(t.ctr);
           mbar_arrive_expect_tx(&bars->c_full[k], L::kRingBytes);
-          tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, BITS ? t.tx0 / 8 : t.tx0, t.ty0, &bars->c_full[k]);
+          tma_load_2d(smem + L::kRing + k * L::kRingBytes, t.ctr, ctr_x(t.tx0), t.ty0, &bars->c_full[k]);
           lseq.next(p);
           issued = j + 1;
         };
@@ -738,7 +876,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           const Tile t = sseq.get(p);
           if (!mbar_wait(&bars->out_full[k], (j / NR) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, t.err, 7); break; }
           if (BATCH || !p.sums) {
-            tma_store_2d(t.out, BITS ? t.tx0 / 8 : t.tx0, t.ty0, smem + L::kRing + k * L::kRingBytes);
+            tma_store_2d(t.out, ctr_x(t.tx0), t.ty0, smem + L::kRing + k * L::kRingBytes);
             bulk_commit();
             bulk_wait_read<0>();          // the store has read the entry
           }
@@ -752,20 +890,38 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     }
   } else if (warp == 3) {
     // ---------------------------------------------------- pass-2 MMA issuer
-    // D2 of tile j over its D1 region once the convert warps have written H.
+    // D2 of tile j once the convert warps have written H: into the D2 region
+    // once the epilogue has read the previous S (wide tile), else over the
+    // tile's own D1 region.
     if (lane == 0) {
-      const uint32_t idesc2 = idesc_f16acc(128, kTile);
-      const uint32_t band16 = tmem + G::kBand16, band8 = tmem + G::kBand8P2;
+      // the wide tile: N = 96 and f32 accumulators (counts up to 4225)
+      const uint32_t idesc2 = WIDE ? idesc_f32acc(128, G::kTS) : idesc_f16acc(128, kTile);
+      const uint32_t band16 = tmem + T::kBand16, band8 = tmem + T::kBand8P2;
+      const uint32_t band_hi = tmem + T::kBand8x16;   // wide tile: the band of 16s for the second digit
       const OpDesc hop0 = op_descs(s_base + L::kH);
       for (int j = 0; j < n_all; ++j) {
+        const int reg = j % ND2;
+        if (DEC && !mbar_wait(&bars->tmem_empty[reg], ((j / ND2) & 1) ^ 1, &bars->abort, p.timeout_ns)) { set_abort(bars, err0, 10); break; }
         if (!mbar_wait(&bars->h_full[j % NH], (j / NH) & 1, &bars->abort, p.timeout_ns)) { set_abort(bars, err0, 9); break; }
         tc_fence_after();
-        const int reg = j % kRegions;
         const uint64_t hoff = (uint64_t)(((j % NH) * L::kHBytes) >> 4);
         const OpDesc hop{hop0.d128 + hoff, hop0.d32 + hoff};
-        const uint32_t d2 = tmem + reg * kRegionCols;
-        if (pass2_f16(DT, tile_rule<BATCH>(p, first, j).r)) band_mma<0, kTile, 2>(d2, band16, hop, idesc2);
-        else band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
+        const uint32_t d2 = tmem + T::kD2Base + reg * T::kD2Cols;
+        const int rj = tile_rule<BATCH>(p, first, j).r;
+        if constexpr (DEC) {
+          // S = band x (H & 15) + (16 band) x (H >> 4), the second only when H
+          // can exceed 15; both e4m3 halves of the H buffer
+          band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
+          if (2 * rj + 1 > 15) {
+            constexpr uint64_t kHi = (uint64_t)((kTile * kWin) >> 4);
+            band_mma<1, kTile, 1, true>(d2, band_hi, OpDesc{hop.d128 + kHi, hop.d32 + kHi}, idesc2);
+          }
+          mma_commit(&bars->h_empty[j % NH]);
+        } else if (pass2_f16(DT, rj)) {
+          band_mma<0, kTile, 2>(d2, band16, hop, idesc2);
+        } else {
+          band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
+        }
         mma_commit(&bars->d2_full[reg]);
       }
       mma_commit(&bars->mma_done[1]);
@@ -793,7 +949,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
     // the bands for the first tile
-    store_bands<DT, SW>(tmem, r0, q, kq, lane);
+    store_bands<DT, SW, WIDE>(tmem, r0, q, kq, lane);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -809,27 +965,38 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         while (ok && enc_next < lim && enc_next / n_my <= j / n_my) ok = encode(enc_next++, wtid, kCvtThreads);
         if (!ok) break;
       }
-      const int reg = j % kRegions;
+      const int reg = j % ND1;
       const int rj = tile_rule<BATCH>(p, first, j).r;
       const bool p2f16 = pass2_f16(DT, rj);
-      // pass 2 of tile j-NH has finished reading this H buffer
-      if (j >= NH && !(ok = warp_wait(&bars->d2_full[(j - NH) % kRegions], ((j - NH) / kRegions) & 1, bars, p.timeout_ns))) break;
+      // pass 2 of tile j-NH has finished reading this H buffer (DEC: it
+      // committed to h_empty; otherwise its D2 is complete, and the region's
+      // next D2 needs this very conversion)
+      if (j >= NH) {
+        if (DEC) ok = warp_wait(&bars->h_empty[j % NH], ((j / NH) & 1) ^ 1, bars, p.timeout_ns);
+        else ok = warp_wait(&bars->d2_full[(j - NH) % ND2], ((j - NH) / ND2) & 1, bars, p.timeout_ns);
+        if (!ok) break;
+      }
       if (BATCH && rj != band_r) {
         // every pass 2 so far (tile j-1 last) has finished reading the bands
-        if (NH > 1 && j >= 1 && !(ok = warp_wait(&bars->d2_full[(j - 1) % kRegions], ((j - 1) / kRegions) & 1, bars, p.timeout_ns))) break;
+        // (and every pass 1: their D1 has been converted)
+        if (NH > 1 && j >= 1) {
+          if (DEC) ok = warp_wait(&bars->h_empty[(j - 1) % NH], ((j - 1) / NH) & 1, bars, p.timeout_ns);
+          else ok = warp_wait(&bars->d2_full[(j - 1) % ND2], ((j - 1) / ND2) & 1, bars, p.timeout_ns);
+          if (!ok) break;
+        }
         tc_fence_after();
-        store_bands<DT, SW>(tmem, rj, q, kq, lane);
+        store_bands<DT, SW, WIDE>(tmem, rj, q, kq, lane);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
         band_r = rj;
       }
-      if (!(ok = warp_wait(&bars->d1_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
+      if (!(ok = warp_wait(&bars->d1_full[reg], (j / ND1) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
       {
         // D1 is f16 (one value per column); packed loads give f16 pairs, which
         // are already the pass-2 operand (or become e4m3 pairs with one cvt)
-        const uint32_t treg = tmem + lane_addr + reg * kRegionCols + 80 * kq;
+        const uint32_t treg = tmem + lane_addr + reg * T::kD1Cols + 80 * kq;
         uint8_t *hop = smem + L::kH + (j % NH) * L::kHBytes;
         // V has kRows columns: 10 chunks of 16, or 9 in a short window (the
         // second warp of a quarter then takes 4)
@@ -839,10 +1006,33 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         for (int c = 0; c < 4; ++c) tmem_ld16_pack16(treg + 16 * c, v[c]);
         if (last) tmem_ld16_pack16(treg + 64, v[4]);
         tmem_wait_ld();
+        if constexpr (DEC) {   // D1 read: pass 1 of tile j + ND1 may overwrite it
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars->d1_empty[reg]);
+        }
+        const bool split = 2 * rj + 1 > 15;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           if (c == 4 && !last) break;
-          if (p2f16) {
+          if constexpr (DEC) {
+            // e4m3 digits H & 15 and H >> 4 (at most 4): each the code of
+            // itself times 2^-9 (e4m3 subnormals for 1..7)
+            const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
+            uint32_t e[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k512, k1024)),
+                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k512, k1024)), 0x6420);
+            *reinterpret_cast<uint4 *>(hop + off8[c]) =
+                make_uint4(e[0] & 0x0F0F0F0Fu, e[1] & 0x0F0F0F0Fu, e[2] & 0x0F0F0F0Fu, e[3] & 0x0F0F0F0Fu);
+            if (split) {
+              uint32_t hi[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) hi[i] = (e[i] >> 4) & 0x0F0F0F0Fu;
+              *reinterpret_cast<uint4 *>(hop + kTile * kWin + off8[c]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            }
+          } else if (p2f16) {
             *reinterpret_cast<uint4 *>(hop + off16a[c]) = make_uint4(v[c][0], v[c][1], v[c][2], v[c][3]);
             *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(v[c][4], v[c][5], v[c][6], v[c][7]);
           } else {
@@ -866,6 +1056,69 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       if (ENC && !MS && j + L::NE < n_all && !(ok = encode(j + L::NE, wtid, kCvtThreads))) break;
     }
     if (!ok) set_abort(bars, err0, 8);
+  } else if constexpr (WIDE) {
+    // ------------------------------------- epilogue warps, wide tile (12 .. 27)
+    // S as f32 (D2, lane y < 96, columns x < 96: six chunks of 16, chunks kq
+    // and kq + 4 per warp) and the centre tile (96-byte rows, no swizzle) ->
+    // next states in place, stored by TMA.  Warps of lane quarter 3 (rows
+    // 96..127, outside the tile) only take part in the barriers.
+    const int q = warp & 3;
+    const int kq = (warp - 4 - kCvtWarps) >> 2;
+    const int y = 32 * q + lane;
+    const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
+    const bool rows = q < 3;
+    const int nch = kq + 4 < 6 ? 2 : 1;
+    bool ok = true;
+    const FloatRule fr = make_float_rule(p.rule, kScale);
+    TileSeq<false, false, G::kTS> seq(p, first, n_my);
+    for (int j = 0; ok && j < n_all; ++j, seq.next(p)) {
+      const int reg = j % ND2, k = j % NR;
+      const Tile t = seq.get(p);
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / ND2) & 1, bars, p.timeout_ns))) break;
+      tc_fence_after();
+      uint32_t v[2][16];                               // S * scale as f32
+      if (rows) {
+        const uint32_t treg = tmem + lane_addr + T::kD2Base + reg * T::kD2Cols;
+        tmem_ld16(treg + 16 * kq, v[0]);
+        if (nch == 2) tmem_ld16(treg + 16 * (kq + 4), v[1]);
+        tmem_wait_ld();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->tmem_empty[reg]);
+      if (!(ok = warp_wait(&bars->c_full[k], (j / NR) & 1, bars, p.timeout_ns))) break;
+      if (rows) {
+        uint8_t *ring = smem + L::kRing + k * L::kRingBytes;
+        for (int c = 0; c < nch; ++c) {
+          const int cc = kq + 4 * c;
+          if (!p.sums) {
+            uint4 *cell = reinterpret_cast<uint4 *>(ring + y * G::kTS + 16 * cc);
+            const uint4 cv = *cell;
+            float f[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[c][i]);
+            uint4 ov;
+            ov.x = rule4_binary_f(f, cv.x, fr);
+            ov.y = rule4_binary_f(f + 4, cv.y, fr);
+            ov.z = rule4_binary_f(f + 8, cv.z, fr);
+            ov.w = rule4_binary_f(f + 12, cv.w, fr);
+            *cell = ov;
+          } else {   // box counts
+            const int gy = t.y0 + y;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int gx = t.x0 + 16 * cc + i;
+              if (gy < t.H && gx < t.W)
+                p.sums[(int64_t)gy * p.sums_ld + gx] = __float2int_rn(__uint_as_float(v[c][i]) * (1.0f / kScale));
+            }
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->out_full[k]);
+    }
+    if (!ok) set_abort(bars, err0, 8);
   } else {
     // ------------------------------------------------ epilogue warps (12 .. 27)
     // S (D2, lane y, columns x) and the centre tile -> next states, written in
@@ -882,19 +1135,19 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     }
     bool ok = true;
     HalfRule hr = make_half_rule(BATCH ? RuleDev{} : p.rule, kScale);
-    TileSeq<BATCH, MS> seq(p, first, n_my);
+    TileSeq<BATCH, MS, G::kTS> seq(p, first, n_my);
     for (int j = 0; ok && j < n_all; ++j, seq.next(p)) {
-      const int reg = j % kRegions, k = j % NR;
+      const int reg = j % ND2, k = j % NR;
       const Tile t = seq.get(p);
       const RuleDev &R = t.R;
       if (BATCH) hr = make_half_rule(R, kScale);
-      if (!(ok = warp_wait(&bars->d2_full[reg], (j / kRegions) & 1, bars, p.timeout_ns))) break;
+      if (!(ok = warp_wait(&bars->d2_full[reg], (j / ND2) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
-      // read S and free the region (the next pass 1 waits for it) before
-      // waiting for the centre tile
+      // read S and free the region (the next pass 1, or in DEC the next pass
+      // 2, waits for it) before waiting for the centre tile
       uint32_t v[2][8];                                // S * scale as f16 pairs
       {
-        const uint32_t treg = tmem + lane_addr + reg * kRegionCols;
+        const uint32_t treg = tmem + lane_addr + T::kD2Base + reg * T::kD2Cols;
         tmem_ld16_pack16(treg + 16 * kq, v[0]);
         tmem_ld16_pack16(treg + 16 * (kq + 4), v[1]);
         tmem_wait_ld();
@@ -917,6 +1170,31 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
             const int lim = t.W - (t.x0 + 16 * cc);
             if (lim < 16) nb &= lim > 0 ? (1u << lim) - 1u : 0u;
             *cellp = (uint16_t)nb;
+          }
+        } else if (NIB && !sums_mode) {
+          // 16 cells of a chunk are 8 bytes of the row, cell 2i in the low
+          // nibble of byte i; the ring row is 64 bytes, 64B-swizzled (16-byte
+          // unit u of row y at u ^ ((y >> 1) & 3)); cells at x >= W stay 0
+          const uint32_t Cb = (uint32_t)R.C * 0x01010101u;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int cc = kq + 4 * c;
+            uint2 *cellp = reinterpret_cast<uint2 *>(ring + y * 64 + ((((cc >> 1) ^ (y >> 1)) & 3) << 4) + 8 * (cc & 1));
+            const uint2 cv = *cellp;
+            const uint32_t st[4] = {nib4_to_bytes(cv.x, 0x4140), nib4_to_bytes(cv.x, 0x4342),
+                                    nib4_to_bytes(cv.y, 0x4140), nib4_to_bytes(cv.y, 0x4342)};
+            uint32_t ns[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              ns[i] = bytes_to_nib_pairs(R.C == 2 ? rule4_binary_h(v[c][2 * i], v[c][2 * i + 1], st[i], hr)
+                                                  : rule4_multistate_h(v[c][2 * i], v[c][2 * i + 1], st[i], hr, Cb));
+            uint2 ov = make_uint2(__byte_perm(ns[0], ns[1], 0x6420), __byte_perm(ns[2], ns[3], 0x6420));
+            const int lim = t.W - (t.x0 + 16 * cc);
+            if (lim < 16) {
+              ov.x = lim >= 8 ? ov.x : lim > 0 ? ov.x & ((1u << (4 * lim)) - 1u) : 0u;
+              ov.y = lim > 8 ? ov.y & ((1u << (4 * (lim - 8))) - 1u) : 0u;
+            }
+            *cellp = ov;
           }
         } else if (!sums_mode && R.C == 2) {
 #pragma unroll
@@ -982,6 +1260,17 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 // single it out.
 __global__ void __launch_bounds__(kThreads, 1) ltl_bits_kernel(const __grid_constant__ TcParams p) {
   ltl_tc_body<1, true, false, false, true, false>(p);
+}
+
+// Four bits per cell (C <= 16): the same body under its own name.
+__global__ void __launch_bounds__(kThreads, 1) ltl_nib_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, true, false, false, false, false, false, true>(p);
+}
+
+// Radii up to 32 (and any radius when asked for): the 96 x 96 tile, single
+// instance, FP8 operands, two-state rules, one step per launch.
+__global__ void __launch_bounds__(kThreads, 1) ltl_wide_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, false, false, false, false, false, true>(p);
 }
 
 // Several steps of a single instance in one cooperative launch (separate
@@ -1337,6 +1626,35 @@ cudaError_t tc_launch(const TcParams &p, int dt, bool encode, bool sw, bool bits
   if (encode) return launch_one<1, true, false>(p, grid, s);
   if (sw) return launch_one<1, false, false, true>(p, grid, s);
   return launch_one<1, false, false>(p, grid, s);
+}
+
+// Four bits per cell: map_in_a is the 96 x 160-byte window map of the packed
+// rows, map_ctr / map_out the 64 x 128-byte tile maps (64B swizzle).
+cudaError_t nib_launch(const TcParams &p, int grid, cudaStream_t s) {
+  static bool configured = false;
+  using L = tc::Layout<1, true, false, false, false, true>;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_nib_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kDyn);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  tc::ltl_nib_kernel<<<grid, tc::kThreads, L::kDyn, s>>>(p);
+  return cudaGetLastError();
+}
+
+// The 96 x 96 tile: map_in_a / map_in_b are the 128 x 160 and 32 x 160 window
+// maps, map_ctr / map_out the 96 x 96 tile maps (no swizzle) of the input and
+// output buffers; tiles_x and n_tiles count 96 x 96 tiles.
+cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s) {
+  static bool configured = false;
+  using L = tc::Layout<1, false, false, false, true>;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kDyn);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  tc::ltl_wide_kernel<<<grid, tc::kThreads, L::kDyn, s>>>(p);
+  return cudaGetLastError();
 }
 
 // Simplified von Neumann neighbourhood: FP8, two-state rules, single instance

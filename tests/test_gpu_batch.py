@@ -92,7 +92,8 @@ def test_batch_multistate_encode_path(cat):
     check_batch(cat, make_batch(4, 20, 16, 400, multistate=True), [4])
 
 
-@pytest.mark.parametrize("kernel,dtype", [("mma_sync", "int8"), ("stencil", "auto"), ("mma_sync", "fp16")])
+@pytest.mark.parametrize("kernel,dtype", [("mma_sync", "int8"), ("stencil", "auto"), ("mma_sync", "fp16"),
+                                          ("runsum", "auto")])
 def test_batch_comparator_kernels(cat, kernel, dtype):
     check_batch(cat, make_batch(5, 10, 16, 300), [3], kernel=kernel, dtype=dtype)
 

@@ -30,7 +30,8 @@ def orule(d):
 
 
 @pytest.mark.parametrize("kernel,dtype,k", [("tcgen05", "fp8", 1), ("tcgen05", "fp8", 3), ("tcgen05", "fp16", 1),
-                                            ("mma_sync", "fp16", 1), ("stencil", "auto", 1)])
+                                            ("mma_sync", "fp16", 1), ("stencil", "auto", 1),
+                                            ("runsum", "auto", 1)])
 def test_steps_on_torch_buffers(cat, kernel, dtype, k):
     import torch
     H, W, pitch = 333, 517, 544            # pitch above the minimum, a multiple of 16

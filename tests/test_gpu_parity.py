@@ -18,7 +18,7 @@ from tests import pins
 pytestmark = pytest.mark.gpu
 
 KERNELS = [("tcgen05", "fp8"), ("tcgen05", "fp16"), ("mma_sync", "fp16"), ("mma_sync", "int8"),
-           ("stencil", "auto")]
+           ("stencil", "auto"), ("runsum", "auto")]
 KIDS = [f"{k}-{d}" for k, d in KERNELS]
 
 

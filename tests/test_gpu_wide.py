@@ -3,9 +3,13 @@
 Beyond the fragment size the paper extends its scheme with a second halo
 fragment and five band fragments per reduction (Sec. VII); the FP16 fragment
 kernel does that, with FP32 accumulation in step 2 since the counts reach
-65^2 = 4225.  The CUDA-core stencil serves these radii too (and the simplified
-von Neumann cross).  The tcgen05 kernels stop at r = 16 and refuse larger
-radii; CAT_KERNEL_AUTO picks the fragment kernel.
+65^2 = 4225.  The tcgen05 kernel serves these radii on 96 x 96 output tiles
+inside the same 160 x 160 window (a 32-cell halo; e4m3 operands, the
+horizontal sums split into H & 15 and H >> 4 against a band of ones and a
+band of 16s, f32 accumulation in pass 2), which CAT_KERNEL_AUTO picks for
+two-state rules.  The CUDA-core stencil serves these radii too (and the
+simplified von Neumann cross).  cat_set_tile also puts radii up to 16 on the
+96 x 96 tile, and short-window radii on the full window.
 """
 import numpy as np
 import pytest
@@ -15,8 +19,8 @@ from paper_2406_17284_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [("mma_sync", "fp16"), ("stencil", "auto"), ("auto", "auto")]
-KIDS = ["mma_sync-fp16", "stencil", "auto"]
+KERNELS = [("tcgen05", "fp8"), ("mma_sync", "fp16"), ("stencil", "auto"), ("runsum", "auto"), ("auto", "auto")]
+KIDS = ["tcgen05-fp8", "mma_sync-fp16", "stencil", "runsum", "auto"]
 RADII = (17, 20, 24, 31, 32)
 
 
@@ -89,6 +93,7 @@ def test_multistate_and_cross(cat):
     want = oracle.step(grid, orule(rule), n_steps=4)
     assert_same(run(cat, "mma_sync", "fp16", grid, rule, 4), want, "C=6 fragment")
     assert_same(run(cat, "stencil", "auto", grid, rule, 4), want, "C=6 stencil")
+    assert_same(run(cat, "runsum", "auto", grid, rule, 4), want, "C=6 running sums")
     cross = inputs.vn_scaled_rule(28)
     g2 = inputs.bernoulli(300, 280, 0.5, 78)
     want = oracle.step(g2, orule(cross), n_steps=3)
@@ -97,10 +102,24 @@ def test_multistate_and_cross(cat):
 
 def test_unsupported(cat):
     rule = inputs.scaled_rule(20)
-    for kernel, dtype in (("tcgen05", "fp8"), ("tcgen05", "fp16"), ("mma_sync", "int8")):
+    for kernel, dtype in (("tcgen05", "fp16"), ("mma_sync", "int8")):
         with pytest.raises(cat.CatError) as e:
             cat.Grid(64, 64, rule, kernel=kernel, dtype=dtype)
         assert e.value.code == cat.CAT_ERR_UNSUPPORTED, (kernel, dtype)
+    for bad in (dict(rule=inputs.scaled_rule(20, C=3)), dict(rule=rule, steps_per_launch=2)):
+        with pytest.raises(cat.CatError) as e:
+            cat.Grid(64, 64, bad["rule"], kernel="tcgen05", dtype="fp8",
+                     steps_per_launch=bad.get("steps_per_launch", 1))
+        assert e.value.code == cat.CAT_ERR_UNSUPPORTED, bad
+    g = cat.Grid(64, 64, rule, kernel="tcgen05", dtype="fp8")
+    try:
+        for args, code in (((128, 128, 0), cat.CAT_ERR_UNSUPPORTED), ((64, 64, 0), cat.CAT_ERR_INVALID_ARG),
+                           ((96, 96, 150), cat.CAT_ERR_INVALID_ARG), ((96, 96, 144), cat.CAT_ERR_UNSUPPORTED)):
+            with pytest.raises(cat.CatError) as e:
+                cat.cat_set_tile(g.handle, *args)
+            assert e.value.code == code, args
+    finally:
+        g.close()
     with pytest.raises(cat.CatError) as e:
         cat.Grid(64, 64, inputs.vn_scaled_rule(20), kernel="mma_sync", dtype="fp16")
     assert e.value.code == cat.CAT_ERR_UNSUPPORTED
@@ -111,8 +130,9 @@ def test_unsupported(cat):
 
 
 def test_full_4096_sampled_windows(cat):
-    """4096^2 Bernoulli(0.5), r = 24 and 32, two steps of the fragment kernel
-    checked on 12 windows (corners included) and equal to the stencil everywhere."""
+    """4096^2 Bernoulli(0.5), r = 24 and 32, two steps of the tcgen05 wide tile
+    checked on 12 windows (corners included) and equal to the stencil and the
+    fragment kernel everywhere."""
     import torch
     N = 4096
     host = inputs.bernoulli(N, N, 0.5, 4242)
@@ -120,17 +140,18 @@ def test_full_4096_sampled_windows(cat):
     rng = np.random.default_rng(3)
     for r in (24, 32):
         rule = inputs.scaled_rule(r)
-        a = cat.Grid(N, N, rule, kernel="mma_sync", dtype="fp16")
+        a = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8")
         b = cat.Grid(N, N, rule, kernel="stencil", dtype="auto")
+        c = cat.Grid(N, N, rule, kernel="mma_sync", dtype="fp16")
         try:
-            a.set_state(d)
-            b.set_state(d)
-            a.step(2)
-            b.step(2)
+            for g in (a, b, c):
+                g.set_state(d)
+                g.step(2)
             torch.cuda.synchronize()
-            assert a.status() == cat.CAT_OK and b.status() == cat.CAT_OK
+            assert a.status() == cat.CAT_OK and b.status() == cat.CAT_OK and c.status() == cat.CAT_OK
             out = a.state_tensor()
-            assert int((out != b.state_tensor()).sum()) == 0, f"r={r}: fragment kernel and stencil differ"
+            assert int((out != b.state_tensor()).sum()) == 0, f"r={r}: tcgen05 wide tile and stencil differ"
+            assert int((out != c.state_tensor()).sum()) == 0, f"r={r}: tcgen05 wide tile and fragment kernel differ"
             spots = [(0, 0), (0, N - 200), (N - 200, 0), (N - 200, N - 200)] + \
                 [tuple(int(v) for v in rng.integers(0, N - 200, 2)) for _ in range(8)]
             for (y0, x0) in spots:
@@ -141,3 +162,36 @@ def test_full_4096_sampled_windows(cat):
         finally:
             a.close()
             b.close()
+            c.close()
+
+
+@pytest.mark.parametrize("r", [1, 5, 8, 13, 16])
+def test_wide_tile_for_small_radii(cat, r):
+    """cat_set_tile(96, 96) on radii up to 16: counts and 3 steps vs the oracle."""
+    grid = inputs.bernoulli(301, 389, 0.45, 900 + r)
+    rule = inputs.scaled_rule(r, M=r % 2)
+    g = cat.Grid(301, 389, rule, kernel="tcgen05", dtype="fp8", tile=96)
+    try:
+        g.set_state(grid)
+        assert_same(g.box_sums(), oracle.box_sums(grid, r), f"S r={r}")
+        g.step(3)
+        assert g.status() == cat.CAT_OK
+        assert_same(g.get_state(), oracle.step(grid, orule(rule), n_steps=3), f"steps r={r}")
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("r", [1, 4, 7])
+def test_full_window_for_short_window_radii(cat, r):
+    """cat_set_tile(0, 0, 160): radii up to 7 on the 160-row window (the
+    standard kernel with its separate D1 and D2 regions) vs the oracle."""
+    grid = inputs.bernoulli(333, 270, 0.5, 700 + r)
+    rule = inputs.scaled_rule(r, M=(r + 1) % 2)
+    g = cat.Grid(333, 270, rule, kernel="tcgen05", dtype="fp8", window=160)
+    try:
+        g.set_state(grid)
+        g.step(3)
+        assert g.status() == cat.CAT_OK
+        assert_same(g.get_state(), oracle.step(grid, orule(rule), n_steps=3), f"r={r}")
+    finally:
+        g.close()

@@ -144,9 +144,9 @@ def test_static_batch_rejections_launch_nothing(cat):
     # no status word: a timeout could not be reported
     assert cat.cat_batch_step_static(descs, cat.DTYPE_FP8_E4M3, None) == cat.CAT_ERR_INVALID_ARG
     assert b"d_status" in cat.load().cat_last_error()
-    # grid 1 writes into grid 0's input
+    # grid 1 writes into grid 2's input
     d1_out = descs[1].out
-    descs[1].out = descs[0].in_ + 16
+    descs[1].out = descs[2].in_ + 16
     assert cat.cat_batch_step_static(descs, cat.DTYPE_FP8_E4M3, status.data_ptr()) == cat.CAT_ERR_INVALID_ARG
     assert b"also uses" in cat.load().cat_last_error()
     # two grids write the same output
