@@ -507,9 +507,9 @@ def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
     per_r = measure_sweep(torch, cat, stream, grids, n)
     ms = sum(per_r.values())
     achieved = 0.25 * n * n * len(RADII) / (ms / 1000.0) / 1e9
-    # the bit-sliced CUDA-core kernel on the same packed grids, r <= 3
+    # the bit-sliced CUDA-core kernel on the same packed grids, r <= 5
     sliced = {}
-    for r in [r for r in RADII if r <= 3]:
+    for r in [r for r in RADII if r <= 5]:
         g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="bitslice", storage=cat.STORE_BIT1)
         g.set_state(d_init)
         g.step(2, stream)

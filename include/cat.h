@@ -107,7 +107,7 @@ enum {
  *         bit x % 8 of byte x / 8 (lowest x in the lowest bit), so a row takes
  *         ceil(W / 8) bytes and the bits past W in the last byte stay 0.  An
  *         eighth of the HBM traffic of U8.  Stepped by the TCGEN05 kernel on
- *         FP8 operands, or by BITSLICE for r <= 3, with the zero boundary
+ *         FP8 operands, or by BITSLICE for r <= 5, with the zero boundary
  *         (Moore neighbourhood); cat_batch_step advances BIT1
  *         instances one launch per instance and step.  The state is still
  *         passed in and out one byte per cell (cat_set_state/cat_get_state
@@ -133,7 +133,7 @@ enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1, CAT_STORE_NIB4 = 2 };
  *             (FP16 operands, or INT8 operands for CAT_DTYPE_INT8).
  *   STENCIL   classical shared-memory CUDA-core stencil (the out-halo SHARED
  *             design of Sec. V-A, Table V), one (2r+1)^2 loop per cell.
- *   BITSLICE  bit-sliced CUDA-core kernel on one-bit storage for r <= 3, the
+ *   BITSLICE  bit-sliced CUDA-core kernel on one-bit storage for r <= 5, the
  *             packed-cell regime where Sec. V-B finds packing faster than
  *             tensor cores: the counts of 32 cells per 32-bit word are added
  *             as bit planes by bitwise full adders, and the rule is a
@@ -165,8 +165,9 @@ typedef struct cat_instance *cat_handle_t;
  * tcgen05 kernel only.  The state is all zero until cat_set_state.  The
  * instance owns its buffers; cat_destroy frees them.  Uses the current CUDA
  * device.  The kernel defaults to TCGEN05 with FP8 operands; r > 16 with C > 2
- * selects MMA_SYNC with FP16 operands, and the simplified von Neumann cross
- * with C > 2 or r > 16 the STENCIL (cat_set_options changes them).  Errors:
+ * selects MMA_SYNC with FP16 operands, the simplified von Neumann cross with
+ * C > 2 or r > 16 the STENCIL, and one-bit storage with r <= 3 BITSLICE
+ * (cat_set_options changes them).  Errors:
  * INVALID_ARG (H or W < 1, H or W > 2^31 - 256, H * pitch > 2^40, bad rule,
  * unknown boundary), UNSUPPORTED (r > 16 with a periodic boundary), OOM,
  * CUDA.                                                                     */
@@ -188,7 +189,7 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).
  * CAT_STORE_BIT1 needs C = 2, the zero boundary and TCGEN05 with FP8_E4M3,
- * or BITSLICE (r <= 3).
+ * or BITSLICE (r <= 5).
  * steps_per_launch = k > 1 makes cat_step run k steps per kernel launch: one
  * cooperative launch (all CTAs resident, one per SM) whose CTAs meet on a
  * grid-wide barrier between steps, so small grids stop paying a launch per
@@ -304,15 +305,16 @@ CAT_API int cat_bind(cat_handle_t h, uint8_t *a, uint8_t *b, int64_t pitch);
 CAT_API int cat_step(cat_handle_t h, int64_t n_steps, void *stream);
 
 /* Advances `count` independent instances by n_steps each.  The instances may
- * differ in size, radius and rule but must share kernel and dtype options.
- * When all of them run the tcgen05 kernel on the Moore neighbourhood with
- * r <= 16, the zero boundary and uint8 storage, each step is ONE persistent
- * launch over a flat tile work-list of all instances, and when `stream` is
- * not capturing the n_steps launches are replayed from a CUDA graph cached
- * for this handle list; otherwise every instance is stepped by its own
- * launches, one step at a time.  Errors: INVALID_ARG (NULL or repeated
- * handles, mixed options), UNSUPPORTED (a batched instance above 4194176
- * cells per side), OOM, CUDA.                                              */
+ * differ in size, radius and rule.  When all of them run the tcgen05 kernel
+ * on the Moore neighbourhood with r <= 16 (128 x 128 tiles), the zero
+ * boundary and uint8 storage, and share the dtype, each step is ONE
+ * persistent launch over a flat tile work-list of all instances, and when
+ * `stream` is not capturing the n_steps launches are replayed from a CUDA
+ * graph cached for this handle list; otherwise every instance is stepped by
+ * its own launches, one step at a time.  Errors: INVALID_ARG (NULL or
+ * repeated handles, instances on different devices, mixed dtypes in a
+ * batched launch), UNSUPPORTED (a batched instance above 4194176 cells per
+ * side), OOM, CUDA.                                                        */
 CAT_API int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void *stream);
 
 /* Debug/verification: writes the counts of the current state, computed by

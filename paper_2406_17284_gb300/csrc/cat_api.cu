@@ -276,21 +276,30 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
 }
 
 // ---------------------------------------------------------------- batches
-// A batch plan: the per-instance descriptor table and the tile work-list of
-// one handle list, kept on the device, plus cached CUDA graphs of n launches.
-struct BatchPlan {
-  std::vector<cat_instance *> hs;
-  std::vector<int> cur0;      // each instance's current buffer when the table was built
-  int64_t steps_done = 0;     // steps advanced through this plan since then
-  int32_t dtype = 0;
-  bool encode = false;
-  bool sw = false;            // every instance qualifies for the short-window kernel
+// A batch plan: the per-instance descriptor tables and tile work-lists of one
+// handle list, kept on the device, plus cached CUDA graphs of n launches.
+// The instances the short-window kernel serves (FP8, C = 2, r <= 7) form one
+// part and the others a second; each part is one persistent launch per step,
+// the two run side by side on disjoint sets of SMs (their CTAs fill one SM
+// each), sized by their tiles' share of the work.
+struct PlanPart {
+  std::vector<int> idx;       // instances of this part (indices into hs)
+  bool sw = false, encode = false;
   cat::BatchInst *d_inst = nullptr;
   cat::BatchTile *d_tiles = nullptr;
   int n_tiles = 0, grid = 0;
+};
+
+struct BatchPlan {
+  std::vector<cat_instance *> hs;
+  std::vector<int> cur0;      // each instance's current buffer when the tables were built
+  int64_t steps_done = 0;     // steps advanced through this plan since then
+  int32_t dtype = 0;
+  PlanPart part[2];           // short-window instances, the others
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // by start parity
   int64_t exec_steps[2] = {0, 0};
-  cudaStream_t capture_stream = nullptr;
+  cudaStream_t capture_stream = nullptr, side_stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 std::mutex g_plan_mu;
@@ -300,8 +309,13 @@ void free_plan(BatchPlan *pl) {
   for (int i = 0; i < 2; ++i)
     if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
   if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
-  cudaFree(pl->d_inst);
-  cudaFree(pl->d_tiles);
+  if (pl->side_stream) cudaStreamDestroy(pl->side_stream);
+  if (pl->fork) cudaEventDestroy(pl->fork);
+  if (pl->join) cudaEventDestroy(pl->join);
+  for (PlanPart &pt : pl->part) {
+    cudaFree(pt.d_inst);
+    cudaFree(pt.d_tiles);
+  }
   delete pl;
 }
 
@@ -317,27 +331,30 @@ void drop_plans_with(cat_instance *h) {
   }
 }
 
-// (Re)writes the instance table of a plan from the handles' current state.
+// (Re)writes the instance tables of a plan from the handles' current state.
 int upload_instances(BatchPlan *pl) {
-  CAT_CUDA(cudaDeviceSynchronize());  // earlier launches of this plan may still read the table
-  std::vector<cat::BatchInst> inst(pl->hs.size());
-  memset(inst.data(), 0, inst.size() * sizeof(cat::BatchInst));
+  CAT_CUDA(cudaDeviceSynchronize());  // earlier launches of this plan may still read the tables
   pl->cur0.resize(pl->hs.size());
-  for (size_t i = 0; i < pl->hs.size(); ++i) {
-    const cat_instance *h = pl->hs[i];
-    for (int b = 0; b < 2; ++b) {
-      inst[i].map_in_a[b] = h->maps[b][pl->sw ? 3 : 0];
-      inst[i].map_in_b[b] = h->maps[b][pl->sw ? 4 : 1];
-      inst[i].map_out[b] = h->maps[b][2];
+  for (PlanPart &pt : pl->part) {
+    if (pt.idx.empty()) continue;
+    std::vector<cat::BatchInst> inst(pt.idx.size());
+    memset(inst.data(), 0, inst.size() * sizeof(cat::BatchInst));
+    for (size_t k = 0; k < pt.idx.size(); ++k) {
+      const cat_instance *h = pl->hs[pt.idx[k]];
+      for (int b = 0; b < 2; ++b) {
+        inst[k].map_in_a[b] = h->maps[b][pt.sw ? 3 : 0];
+        inst[k].map_in_b[b] = h->maps[b][pt.sw ? 4 : 1];
+        inst[k].map_out[b] = h->maps[b][2];
+      }
+      inst[k].rule = h->rd;
+      inst[k].H = (int32_t)h->H;
+      inst[k].W = (int32_t)h->W;
+      inst[k].cur = h->cur;
+      inst[k].err = h->d_err;
+      pl->cur0[pt.idx[k]] = h->cur;
     }
-    inst[i].rule = h->rd;
-    inst[i].H = (int32_t)h->H;
-    inst[i].W = (int32_t)h->W;
-    inst[i].cur = h->cur;
-    inst[i].err = h->d_err;
-    pl->cur0[i] = h->cur;
+    CAT_CUDA(cudaMemcpy(pt.d_inst, inst.data(), inst.size() * sizeof(cat::BatchInst), cudaMemcpyHostToDevice));
   }
-  CAT_CUDA(cudaMemcpy(pl->d_inst, inst.data(), inst.size() * sizeof(cat::BatchInst), cudaMemcpyHostToDevice));
   pl->steps_done = 0;
   for (int i = 0; i < 2; ++i) {
     if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
@@ -352,28 +369,47 @@ int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
   if (!pl) return fail(CAT_ERR_OOM, "host allocation failed");
   pl->hs.assign(hs, hs + count);
   pl->dtype = hs[0]->dtype;
-  pl->encode = false;
-  for (int32_t i = 0; i < count; ++i) pl->encode |= hs[i]->rule.C > 2;
-  pl->sw = true;
-  for (int32_t i = 0; i < count; ++i) pl->sw &= short_window(hs[i]);
-  // work-list: instances ordered by radius, tiles row-major within an instance
+  // part 0: the short-window instances; part 1: the others.  Work-lists are
+  // ordered by radius (the kernel rebuilds its bands when r changes), tiles
+  // row-major within an instance.
   std::vector<int> order(count);
   for (int32_t i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->rule.r < hs[b]->rule.r; });
-  std::vector<cat::BatchTile> tiles;
-  for (int i : order) {
-    const int64_t ty = (hs[i]->H + 127) / 128, tx = (hs[i]->W + 127) / 128;
-    for (int64_t y = 0; y < ty; ++y)
-      for (int64_t x = 0; x < tx; ++x) tiles.push_back(cat::BatchTile{i, (int16_t)y, (int16_t)x});
+  for (int i : order) pl->part[short_window(hs[i]) ? 0 : 1].idx.push_back(i);
+  pl->part[0].sw = true;
+  std::vector<cat::BatchTile> tiles[2];
+  for (int k = 0; k < 2; ++k) {
+    PlanPart &pt = pl->part[k];
+    for (size_t j = 0; j < pt.idx.size(); ++j) {
+      const cat_instance *h = hs[pt.idx[j]];
+      pt.encode |= h->rule.C > 2;
+      const int64_t ty = (h->H + 127) / 128, tx = (h->W + 127) / 128;
+      for (int64_t y = 0; y < ty; ++y)
+        for (int64_t x = 0; x < tx; ++x) tiles[k].push_back(cat::BatchTile{(int32_t)j, (int16_t)y, (int16_t)x});
+    }
+    if (tiles[k].size() > (size_t)INT32_MAX) { delete pl; return fail(CAT_ERR_UNSUPPORTED, "batch too large"); }
+    pt.n_tiles = (int)tiles[k].size();
   }
-  if (tiles.size() > (size_t)INT32_MAX) { delete pl; return fail(CAT_ERR_UNSUPPORTED, "batch too large"); }
-  pl->n_tiles = (int)tiles.size();
-  pl->grid = std::min(pl->n_tiles, hs[0]->dev.sms);
-  cudaError_t e = cudaMalloc(&pl->d_inst, sizeof(cat::BatchInst) * count);
-  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tiles, sizeof(cat::BatchTile) * tiles.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_tiles, tiles.data(), sizeof(cat::BatchTile) * tiles.size(), cudaMemcpyHostToDevice);
+  // SMs by work: a short-window tile costs about 0.8 of a standard one
+  const int sms = hs[0]->dev.sms;
+  const double w0 = 0.8 * pl->part[0].n_tiles, w1 = pl->part[1].n_tiles;
+  int g0 = pl->part[1].n_tiles == 0 ? sms : pl->part[0].n_tiles == 0 ? 0 : (int)(sms * w0 / (w0 + w1) + 0.5);
+  g0 = std::max(pl->part[0].n_tiles ? 1 : 0, std::min(g0, sms - (pl->part[1].n_tiles ? 1 : 0)));
+  pl->part[0].grid = std::min(pl->part[0].n_tiles, g0);
+  pl->part[1].grid = std::min(pl->part[1].n_tiles, sms - g0);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    PlanPart &pt = pl->part[k];
+    if (pt.idx.empty()) continue;
+    e = cudaMalloc(&pt.d_inst, sizeof(cat::BatchInst) * pt.idx.size());
+    if (e == cudaSuccess) e = cudaMalloc(&pt.d_tiles, sizeof(cat::BatchTile) * tiles[k].size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pt.d_tiles, tiles[k].data(), sizeof(cat::BatchTile) * tiles[k].size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming);
   if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "batch plan"); }
   int rc = upload_instances(pl);
   if (rc) { free_plan(pl); return rc; }
@@ -381,17 +417,34 @@ int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
   return CAT_OK;
 }
 
+// n_steps steps of every instance: each part's launches in order on its own
+// stream (part 0 on `s`, part 1 on a side stream forked from and joined back
+// into `s`); the parts share no grid, so they need not meet between steps.
 int launch_batch_steps(BatchPlan *pl, int64_t n_steps, int64_t start, cudaStream_t s) {
-  cat::TcParams p;
-  memset(&p, 0, sizeof(p));
-  p.n_tiles = pl->n_tiles;
-  p.timeout_ns = pl->hs[0]->timeout_ns;
-  p.binst = pl->d_inst;
-  p.btiles = pl->d_tiles;
-  for (int64_t t = 0; t < n_steps; ++t) {
-    p.parity = (int32_t)((start + t) & 1);
-    cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pl->encode, pl->sw, pl->grid, s);
-    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  const bool both = !pl->part[0].idx.empty() && !pl->part[1].idx.empty();
+  if (both) {
+    CAT_CUDA(cudaEventRecord(pl->fork, s));
+    CAT_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->fork, 0));
+  }
+  for (int k = 0; k < 2; ++k) {
+    const PlanPart &pt = pl->part[k];
+    if (pt.idx.empty()) continue;
+    const cudaStream_t ps = (both && k == 1) ? pl->side_stream : s;
+    cat::TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_tiles = pt.n_tiles;
+    p.timeout_ns = pl->hs[0]->timeout_ns;
+    p.binst = pt.d_inst;
+    p.btiles = pt.d_tiles;
+    for (int64_t t = 0; t < n_steps; ++t) {
+      p.parity = (int32_t)((start + t) & 1);
+      cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pt.encode, pt.sw, pt.grid, ps);
+      if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    }
+  }
+  if (both) {
+    CAT_CUDA(cudaEventRecord(pl->join, pl->side_stream));
+    CAT_CUDA(cudaStreamWaitEvent(s, pl->join, 0));
   }
   return CAT_OK;
 }
@@ -577,6 +630,9 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   } else if (rule->r > 16 && rule->C > 2) {  // the paper's fragment scheme with two halo fragments
     h->kernel = CAT_KERNEL_MMA_SYNC;
     h->dtype = CAT_DTYPE_FP16;
+  } else if (storage == CAT_STORE_BIT1 && rule->r <= 3) {  // packed cells at small r: bit planes on CUDA cores
+    h->kernel = CAT_KERNEL_BITSLICE;
+    h->dtype = CAT_DTYPE_AUTO;
   }   // r > 16 with C = 2: the tcgen05 wide tile
   const size_t bytes = (size_t)(h->pitch * (H + 2 * h->ghost));
   cudaError_t e = cudaMalloc(&h->buf[0], bytes);
@@ -623,9 +679,10 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
     }
   }
   if (kernel == CAT_KERNEL_AUTO)
-    kernel = vn && (h->rule.C > 2 || wide) ? CAT_KERNEL_STENCIL
-           : wide && h->rule.C > 2         ? CAT_KERNEL_MMA_SYNC
-                                           : CAT_KERNEL_TCGEN05;
+    kernel = vn && (h->rule.C > 2 || wide)                                ? CAT_KERNEL_STENCIL
+           : wide && h->rule.C > 2                                        ? CAT_KERNEL_MMA_SYNC
+           : storage == CAT_STORE_BIT1 && h->rule.r <= 3 && h->rule.C == 2 ? CAT_KERNEL_BITSLICE
+                                                                          : CAT_KERNEL_TCGEN05;
   const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
   if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
@@ -637,9 +694,9 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_RUNSUM && vn)
     return fail(CAT_ERR_UNSUPPORTED, "the running-sum kernel serves the Moore neighbourhood");
   if (kernel == CAT_KERNEL_BITSLICE) {   // bitwise adders on CUDA cores: no operand dtype
-    if (storage != CAT_STORE_BIT1 || h->rule.C != 2 || vn || h->ghost || h->rule.r > 3)
+    if (storage != CAT_STORE_BIT1 || h->rule.C != 2 || vn || h->ghost || h->rule.r > 5)
       return fail(CAT_ERR_UNSUPPORTED, "the bit-sliced kernel serves one-bit storage, two-state Moore rules, "
-                                       "the zero boundary and r <= 3");
+                                       "the zero boundary and r <= 5");
     dtype = CAT_DTYPE_AUTO;
   }
   // the 96 x 96 tile: radii above 16 on tcgen05, or any radius after cat_set_tile(96, 96)
@@ -788,10 +845,15 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   for (int32_t i = 0; i < count; ++i) {
     all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8 &&
               hs[i]->rule.nbhd == 'M' && !wide_tile(hs[i]);
-    if (hs[i]->kernel != hs[0]->kernel || hs[i]->dtype != hs[0]->dtype || hs[i]->dev.id != hs[0]->dev.id)
-      return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share kernel, dtype and device");
-    if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)
-      return fail(CAT_ERR_UNSUPPORTED, "batched instances are limited to 4194176 x 4194176 cells");
+    if (hs[i]->dev.id != hs[0]->dev.id) return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share the device");
+  }
+  if (all_tc) {   // one persistent launch over every instance: one kernel instantiation
+    for (int32_t i = 0; i < count; ++i) {
+      if (hs[i]->dtype != hs[0]->dtype)
+        return fail(CAT_ERR_INVALID_ARG, "instances of a batched tcgen05 launch must share the dtype");
+      if (hs[i]->H > 128 * 32767 || hs[i]->W > 128 * 32767)
+        return fail(CAT_ERR_UNSUPPORTED, "batched instances are limited to 4194176 x 4194176 cells");
+    }
   }
   if (!all_tc) {  // the comparator kernels have no batched launch: one launch per instance and step
     for (int64_t t = 0; t < n_steps; ++t)

@@ -47,7 +47,10 @@ __device__ __forceinline__ uint32_t alive4(uint32_t w) {
 }
 
 // Stages alive flags of window rows [y0 - r, y0 + BY + r) x columns
-// [x0 - 32, x0 + 160) into A (row stride WX) and the raw centre tile into ctr.
+// [x0 - 32, x0 + 160) into A (row stride WX) and the raw centre tile into ctr
+// (row stride CS: BX, or BX + 4 so that threads reading down a column of
+// rows hit different banks).
+template <int CS>
 __device__ __forceinline__ void stage(const SimpleParams &p, int x0, int y0, int r, uint8_t *A, uint8_t *ctr) {
   const int rows = BY + 2 * r;
   for (int i = threadIdx.x; i < rows * (WX / 16); i += kThreads) {
@@ -67,8 +70,15 @@ __device__ __forceinline__ void stage(const SimpleParams &p, int x0, int y0, int
         v = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
-    if (wy >= r && wy < r + BY && c >= 2 && c < 10)
-      *reinterpret_cast<uint4 *>(ctr + (wy - r) * BX + 16 * (c - 2)) = v;
+    if (wy >= r && wy < r + BY && c >= 2 && c < 10) {
+      uint8_t *dst = ctr + (wy - r) * CS + 16 * (c - 2);
+      if constexpr (CS % 16 == 0) {
+        *reinterpret_cast<uint4 *>(dst) = v;
+      } else {
+        uint32_t *d4 = reinterpret_cast<uint32_t *>(dst);
+        d4[0] = v.x; d4[1] = v.y; d4[2] = v.z; d4[3] = v.w;
+      }
+    }
     if (p.rule.C > 2) v = make_uint4(alive4(v.x), alive4(v.y), alive4(v.z), alive4(v.w));
     *reinterpret_cast<uint4 *>(A + wy * WX + 16 * c) = v;
   }
@@ -90,23 +100,24 @@ __global__ void __launch_bounds__(kThreads) smem_stencil_kernel(const SimplePara
   __shared__ __align__(16) uint8_t ctr[BY * BX];
   const int r = p.rule.r;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  stage(p, x0, y0, r, A, ctr);
+  stage<BX>(p, x0, y0, r, A, ctr);
   __syncthreads();
-  // thread: row y of the tile and a 32-cell segment k, eight words of four cells
-  const int k = threadIdx.x & 3, y = threadIdx.x >> 2;
-  const int gy = y0 + y, gx = x0 + 32 * k;
-  if (gy >= p.H || gx >= p.W) return;
-  uint32_t o[8];
-#pragma unroll 1
-  for (int q = 0; q < 8; ++q) {
-    const int xw = 32 + 32 * k + 4 * q;   // window column of the word's first cell
+  // lane q: the word of four cells 4q .. 4q + 3 of a row (consecutive lanes
+  // read consecutive words, so no bank conflicts); warp w: rows w, w + 8, ...
+  const int q = threadIdx.x & 31, w8 = threadIdx.x >> 5;
+  const int gx = x0 + 4 * q;
+  if (gx >= p.W) return;
+  const int xw = 32 + 4 * q;              // window column of the word's first cell
+  for (int y = w8; y < BY; y += kThreads / 32) {
+    const int gy = y0 + y;
+    if (gy >= p.H) break;
     uint32_t s01 = 0, s23 = 0;            // counts of cells 0,1 and 2,3 as 16-bit pairs
     if (p.rule.nbhd) {                    // Eq. 3: vertical and horizontal segment
       uint32_t h = 0;
+      const uint32_t *row = reinterpret_cast<const uint32_t *>(A + (y + r) * WX);
       for (int d = 0; d <= 2 * r; ++d) {
         h += *reinterpret_cast<const uint32_t *>(A + (y + d) * WX + xw);
         const int b = xw - r + d, j = b >> 2;
-        const uint32_t *row = reinterpret_cast<const uint32_t *>(A + (y + r) * WX);
         h += __funnelshift_r(row[j], row[j + 1], 8 * (b & 3));
       }
       s01 = __byte_perm(h, 0, 0x4140);
@@ -123,29 +134,34 @@ __global__ void __launch_bounds__(kThreads) smem_stencil_kernel(const SimplePara
         s23 += __byte_perm(h, 0, 0x4342);
       }
     }
-    const int s[4] = {(int)(s01 & 0xFFFF), (int)(s01 >> 16), (int)(s23 & 0xFFFF), (int)(s23 >> 16)};
+    const int sv[4] = {(int)(s01 & 0xFFFF), (int)(s01 >> 16), (int)(s23 & 0xFFFF), (int)(s23 >> 16)};
+    if (p.sums) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (gx + t < p.W) p.sums[(int64_t)gy * p.sums_ld + gx + t] = sv[t];
+      continue;
+    }
+    const uint32_t cw = *reinterpret_cast<const uint32_t *>(ctr + y * BX + 4 * q);
     uint32_t w = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int x = 32 * k + 4 * q + t;
-      if (p.sums) {
-        if (gx + 4 * q + t < p.W) p.sums[(int64_t)gy * p.sums_ld + gx + 4 * q + t] = s[t];
-      } else {
-        w |= next_state(s[t], ctr[y * BX + x], p.rule) << (8 * t);
-      }
+    for (int t = 0; t < 4; ++t) w |= next_state(sv[t], (cw >> (8 * t)) & 0xFFu, p.rule) << (8 * t);
+    uint8_t *dst = p.out + (int64_t)gy * p.pitch + gx;
+    if (gx + 4 <= p.W) {
+      *reinterpret_cast<uint32_t *>(dst) = w;
+    } else {
+      for (int t = 0; gx + t < p.W; ++t) dst[t] = (uint8_t)(w >> (8 * t));
     }
-    o[q] = w;
   }
-  if (!p.sums) store32(p, gy, gx, o);
 }
 
 __global__ void __launch_bounds__(kThreads) runsum_kernel(const SimpleParams p) {
+  constexpr int CS = BX + 4;   // centre rows 132 bytes apart: the 32 lanes' byte reads hit 32 banks
   __shared__ __align__(16) uint8_t A[WY * WX];
-  __shared__ __align__(16) uint8_t ctr[BY * BX];
+  __shared__ __align__(16) uint8_t ctr[BY * CS];
   __shared__ __align__(16) uint8_t V[BY * VX];
   const int r = p.rule.r;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  stage(p, x0, y0, r, A, ctr);
+  stage<CS>(p, x0, y0, r, A, ctr);
   __syncthreads();
   // vertical running sums, four columns per word: 48 word columns x 4 segments of 16 rows
   if (threadIdx.x < (WX / 4) * (BY / 16)) {
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) runsum_kernel(const SimpleParams p) 
   int s = 0;
   for (int d = -r; d <= r; ++d) s += vr[d];
   uint32_t o[8];
-  const uint8_t *cr = ctr + y * BX + 32 * k;
+  const uint8_t *cr = ctr + y * CS + 32 * k;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     uint32_t w = 0;

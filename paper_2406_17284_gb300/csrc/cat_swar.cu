@@ -1,4 +1,4 @@
-// Bit-sliced (SWAR) Larger-than-Life step on one-bit storage, radii 1..3.
+// Bit-sliced (SWAR) Larger-than-Life step on one-bit storage, radii 1..5.
 //
 // At the smallest radii the paper finds its packed-cell comparator faster
 // than the tensor-core method (Sec. V-B: at r = 1 the packed program beats
@@ -16,8 +16,8 @@
 //               numbers added (the horizontal sums of a thread's rows are
 //               kept in registers while it walks down its strip);
 //   rule        S in [lo, lo + w] for the survival and birth ranges of the
-//               reduced rule, each bound a bit-serial comparison with a
-//               constant; the centre bit picks survival or birth.
+//               reduced rule, each bound the carry chain of a bit-sliced
+//               addition of a constant; the centre bit picks survival or birth.
 //
 // S is the Moore box count with the centre (Sec. IV, Eqs. 1-2 compute the
 // same number as band products); the reduced rule's survival bounds already
@@ -35,11 +35,16 @@ namespace {
 constexpr int kRows = 32;        // output rows per thread
 constexpr int kBlock = 256;      // threads: 8 warps side by side, 256 words
 
+// Bits needed for a value up to n.
+constexpr int bits_for(int n) { return n < 2 ? 1 : 1 + bits_for(n / 2); }
+
 template <int R>
 struct Bits {
-  static constexpr int kH = 2 * R + 1 <= 3 ? 2 : 3;                         // bits of a horizontal sum
-  static constexpr int kS = (2 * R + 1) * (2 * R + 1) < 16 ? 4 : (2 * R + 1) * (2 * R + 1) < 32 ? 5 : 6;
+  static constexpr int kH = bits_for(2 * R + 1);                 // bits of a horizontal sum
+  static constexpr int kS = bits_for((2 * R + 1) * (2 * R + 1));  // bits of a box count
 };
+static_assert(Bits<1>::kH == 2 && Bits<1>::kS == 4 && Bits<2>::kS == 5 && Bits<3>::kS == 6 && Bits<5>::kS == 7,
+              "plane counts");
 
 // acc += x (bit-sliced, NX-bit x into an NB-bit accumulator).
 template <int NB, int NX>
@@ -54,30 +59,50 @@ __device__ __forceinline__ void bs_add(uint32_t (&acc)[NB], const uint32_t (&x)[
   }
 }
 
-// Plane of the cells whose count S >= K (K uniform across the grid).
+// S >= K for every cell of a word, as the carry out of the bit-sliced sum
+// S + (2^NB - K): one majority function per bit, carry = maj(S_b, carry, k_b),
+// where k_b is bit b of 2^NB - K replicated over a word (0 or ~0).  K <= 0 and
+// K >= 2^NB are settled by the caller.
 template <int NB>
-__device__ __forceinline__ uint32_t bs_ge(const uint32_t (&S)[NB], int K) {
-  if (K <= 0) return ~0u;
-  if (K >= (1 << NB)) return 0u;
-  uint32_t gt = 0, eq = ~0u;
+__device__ __forceinline__ uint32_t bs_ge(const uint32_t (&S)[NB], const uint32_t (&k)[NB]) {
+  uint32_t carry = 0;
 #pragma unroll
-  for (int b = NB - 1; b >= 0; --b) {
-    if ((K >> b) & 1) {
-      eq &= S[b];
-    } else {
-      gt |= eq & S[b];
-      eq &= ~S[b];
-    }
-  }
-  return gt | eq;
+  for (int b = 0; b < NB; ++b) carry = (S[b] & carry) | (k[b] & (S[b] | carry));
+  return carry;
 }
 
-// Plane of the cells whose count lies in [lo, lo + w].
+// One range [lo, lo + w] of the reduced rule as the constants of two carry
+// chains: in range iff S >= lo and not S >= lo + w + 1, with the chains that
+// can never or must always carry replaced by fixed words.
 template <int NB>
-__device__ __forceinline__ uint32_t bs_in(const uint32_t (&S)[NB], int lo, int w) {
-  if (lo >= (1 << NB)) return 0u;
-  const int64_t end = (int64_t)lo + w + 1;                     // first count above the range
-  return bs_ge<NB>(S, lo) & (end >= (1 << NB) ? ~0u : ~bs_ge<NB>(S, (int)end));
+struct RangeBits {
+  uint32_t klo[NB], khi[NB];
+  uint32_t lo_fix_and, lo_fix_or, hi_fix_and, hi_fix_or;
+};
+
+template <int NB>
+__device__ __forceinline__ void bound_bits(int64_t K, uint32_t (&k)[NB], uint32_t &fix_and, uint32_t &fix_or) {
+  // K <= 0: always >= K (or 1); K >= 2^NB: never (and 0); else the chain
+  const int64_t c = (int64_t(1) << NB) - K;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) k[b] = (K > 0 && K < (int64_t(1) << NB) && ((c >> b) & 1)) ? ~0u : 0u;
+  fix_and = (K > 0 && K < (int64_t(1) << NB)) ? ~0u : 0u;
+  fix_or = K <= 0 ? ~0u : 0u;
+}
+
+template <int NB>
+__device__ __forceinline__ RangeBits<NB> range_bits(int lo, int w) {
+  RangeBits<NB> rb;
+  bound_bits<NB>(lo, rb.klo, rb.lo_fix_and, rb.lo_fix_or);
+  bound_bits<NB>((int64_t)lo + w + 1, rb.khi, rb.hi_fix_and, rb.hi_fix_or);
+  return rb;
+}
+
+template <int NB>
+__device__ __forceinline__ uint32_t bs_in(const uint32_t (&S)[NB], const RangeBits<NB> &rb) {
+  const uint32_t ge_lo = (bs_ge<NB>(S, rb.klo) & rb.lo_fix_and) | rb.lo_fix_or;
+  const uint32_t ge_hi = (bs_ge<NB>(S, rb.khi) & rb.hi_fix_and) | rb.hi_fix_or;
+  return ge_lo & ~ge_hi;
 }
 
 struct SwarParams {
@@ -97,20 +122,25 @@ __global__ void __launch_bounds__(kBlock) ltl_swar_kernel(const SwarParams p) {
   const int wi = blockIdx.x * kBlock + threadIdx.x;             // word column
   const bool col = wi < p.words;
   const int last_bits = p.W - 32 * (p.words - 1);                 // valid bits of the last word
-  const uint32_t mask = (wi == p.words - 1 && last_bits < 32) ? (1u << last_bits) - 1u : ~0u;
+  const uint32_t last_mask = last_bits < 32 ? (1u << last_bits) - 1u : ~0u;
+  const uint32_t mask = wi == p.words - 1 ? last_mask : ~0u;
+  // the neighbour word this lane loads besides its own: lane 0 the one to the
+  // left of the warp, lane 31 the one to the right (a warp covers 32 words)
+  const int nc = lane == 0 ? wi - 1 : lane == 31 ? wi + 1 : wi;
+  const bool nc_ok = nc >= 0 && nc < p.words;
+  const uint32_t nmask = nc == p.words - 1 ? last_mask : ~0u;
+  const uint32_t *in_c = p.in + (col ? wi : 0), *in_n = p.in + (nc_ok ? nc : 0);
+  const RangeBits<NS> surv = range_bits<NS>(p.rule.s_lo, p.rule.s_w), born = range_bits<NS>(p.rule.b_lo, p.rule.b_w);
 
-  // the word of row y at column c, 0 outside the grid
-  auto word = [&](int y, int c) -> uint32_t {
-    if (y < 0 || y >= p.H || c < 0 || c >= p.words) return 0u;
-    const uint32_t v = __ldg(p.in + (int64_t)y * p.pitch_words + c);
-    return c == p.words - 1 && last_bits < 32 ? v & ((1u << last_bits) - 1u) : v;
-  };
   // horizontal sums of row y for this thread's 32 cells (every lane takes part)
   auto hsum = [&](int y, uint32_t (&h)[NH], uint32_t &centre) {
-    const uint32_t w = col ? word(y, wi) : 0u;
+    const bool row_ok = y >= 0 && y < p.H;
+    const int64_t ro = row_ok ? (int64_t)y * p.pitch_words : 0;
+    const uint32_t w = (row_ok && col) ? __ldg(in_c + ro) & mask : 0u;
+    const uint32_t x = (row_ok && nc_ok) ? __ldg(in_n + ro) & nmask : 0u;
     uint32_t left = __shfl_up_sync(0xffffffffu, w, 1), right = __shfl_down_sync(0xffffffffu, w, 1);
-    if (lane == 0) left = word(y, wi - 1);
-    if (lane == 31) right = word(y, wi + 1);
+    if (lane == 0) left = x;
+    if (lane == 31) right = x;
 #pragma unroll
     for (int b = 0; b < NH; ++b) h[b] = 0u;
     const uint32_t w1[1] = {w};
@@ -125,42 +155,40 @@ __global__ void __launch_bounds__(kBlock) ltl_swar_kernel(const SwarParams p) {
     centre = w;
   };
 
-  const RuleDev &rd = p.rule;
   // strips of kRows rows, grid-stride in y (grids taller than 65535 strips)
   for (int64_t y0 = (int64_t)blockIdx.y * kRows; y0 < p.H; y0 += (int64_t)gridDim.y * kRows) {
-  uint32_t hs[WIN][NH], cs[WIN];
+    uint32_t hs[WIN][NH], cs[WIN];
 #pragma unroll
-  for (int k = 0; k < WIN - 1; ++k) hsum((int)y0 - R + k, hs[k + 1], cs[k + 1]);
-  for (int i = 0; i < kRows; ++i) {
-    const int y = (int)y0 + i;
-    if (y >= p.H) break;                                          // uniform across the block
+    for (int k = 0; k < WIN - 1; ++k) hsum((int)y0 - R + k, hs[k + 1], cs[k + 1]);
+    for (int i = 0; i < kRows; ++i) {
+      const int y = (int)y0 + i;
+      if (y >= p.H) break;                                        // uniform across the block
 #pragma unroll
-    for (int k = 0; k < WIN - 1; ++k) {
+      for (int k = 0; k < WIN - 1; ++k) {
 #pragma unroll
-      for (int b = 0; b < NH; ++b) hs[k][b] = hs[k + 1][b];
-      cs[k] = cs[k + 1];
-    }
-    hsum(y + R, hs[WIN - 1], cs[WIN - 1]);
-    uint32_t S[NS];
-#pragma unroll
-    for (int b = 0; b < NS; ++b) S[b] = b < NH ? hs[0][b] : 0u;
-#pragma unroll
-    for (int k = 1; k < WIN; ++k) bs_add<NS, NH>(S, hs[k]);
-    if (!col) continue;
-    const uint32_t c = cs[R];
-    if (p.sums) {
-      int32_t *row = p.sums + (int64_t)y * p.sums_ld;
-      for (int t = 0; t < 32 && 32 * wi + t < p.W; ++t) {
-        int v = 0;
-#pragma unroll
-        for (int b = 0; b < NS; ++b) v |= (int)((S[b] >> t) & 1u) << b;
-        row[32 * wi + t] = v;
+        for (int b = 0; b < NH; ++b) hs[k][b] = hs[k + 1][b];
+        cs[k] = cs[k + 1];
       }
-      continue;
+      hsum(y + R, hs[WIN - 1], cs[WIN - 1]);
+      uint32_t S[NS];
+#pragma unroll
+      for (int b = 0; b < NS; ++b) S[b] = b < NH ? hs[0][b] : 0u;
+#pragma unroll
+      for (int k = 1; k < WIN; ++k) bs_add<NS, NH>(S, hs[k]);
+      if (!col) continue;
+      const uint32_t c = cs[R];
+      if (p.sums) {
+        int32_t *row = p.sums + (int64_t)y * p.sums_ld;
+        for (int t = 0; t < 32 && 32 * wi + t < p.W; ++t) {
+          int v = 0;
+#pragma unroll
+          for (int b = 0; b < NS; ++b) v |= (int)((S[b] >> t) & 1u) << b;
+          row[32 * wi + t] = v;
+        }
+        continue;
+      }
+      p.out[(int64_t)y * p.pitch_words + wi] = ((c & bs_in<NS>(S, surv)) | (~c & bs_in<NS>(S, born))) & mask;
     }
-    const uint32_t surv = bs_in<NS>(S, rd.s_lo, rd.s_w), born = bs_in<NS>(S, rd.b_lo, rd.b_w);
-    p.out[(int64_t)y * p.pitch_words + wi] = ((c & surv) | (~c & born)) & mask;
-  }
   }
 }
 
@@ -184,6 +212,8 @@ cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t 
     case 1: ltl_swar_kernel<1><<<grid, kBlock, 0, s>>>(p); break;
     case 2: ltl_swar_kernel<2><<<grid, kBlock, 0, s>>>(p); break;
     case 3: ltl_swar_kernel<3><<<grid, kBlock, 0, s>>>(p); break;
+    case 4: ltl_swar_kernel<4><<<grid, kBlock, 0, s>>>(p); break;
+    case 5: ltl_swar_kernel<5><<<grid, kBlock, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

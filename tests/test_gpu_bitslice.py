@@ -1,5 +1,5 @@
 """The bit-sliced CUDA-core kernel (CAT_KERNEL_BITSLICE, one-bit storage,
-r <= 3) vs the CPU oracle, element by element.
+r <= 5) vs the CPU oracle, element by element.
 
 The kernel adds the counts of 32 cells per word as bit planes; every case
 below checks the funnel-shifted neighbours across word and warp boundaries,
@@ -70,7 +70,7 @@ def run(cat, grid, rule, steps):
 SHAPES = [(1, 1), (1, 33), (3, 31), (5, 32), (77, 100), (40, 1025), (130, 8200), (33, 64)]
 
 
-@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 def test_counts(cat, r):
     for i, (H, W) in enumerate(SHAPES):
         grid = inputs.bernoulli(H, W, 0.5, 50 + 7 * i + r)
@@ -99,14 +99,14 @@ def test_conway_patterns_and_100_steps(cat):
     assert after4[21, 30] == 1 and after4[23, 29:32].all()
 
 
-@pytest.mark.parametrize("rule", table_iv(3), ids=lambda d: f"r{d['r']}")
+@pytest.mark.parametrize("rule", table_iv(5), ids=lambda d: f"r{d['r']}")
 def test_table_iv_rules(cat, rule):
     for i, (H, W) in enumerate([(200, 300), (65, 1000), (1, 70)]):
         grid = inputs.bernoulli(H, W, 0.3 + 0.1 * i, 300 + i + rule["r"])
         assert_same(run(cat, grid, rule, 5), oracle.step(grid, orule(rule), n_steps=5), f"{H}x{W}")
 
 
-@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("M", [0, 1])
 def test_scaled_rules_and_empty_ranges(cat, r, M):
     grid = inputs.bernoulli(181, 517, 0.5, 10 * r + M)
@@ -146,7 +146,7 @@ def test_full_16384_equals_tcgen05_bits_and_oracle_windows(cat):
 
 
 def test_unsupported(cat):
-    for rule, kw in ((inputs.scaled_rule(4), dict(storage=cat.STORE_BIT1)),
+    for rule, kw in ((inputs.scaled_rule(6), dict(storage=cat.STORE_BIT1)),
                      (inputs.scaled_rule(2), dict(storage=cat.STORE_U8)),
                      (inputs.vn_scaled_rule(2), dict(storage=cat.STORE_U8))):
         with pytest.raises(cat.CatError) as e:
