@@ -459,7 +459,9 @@ def measure_vn(args, torch, cat, inputs, stream, d_init, hbm):
 def measure_multistep(torch, cat, inputs, stream, steps=64):
     """Small single grids (L2-resident), the scaled rule r = 4 (FP8): `steps` steps with
     one launch per step (cat_step, k = 1) and with all of them in one cooperative
-    launch (k = steps, CTAs meeting on a grid barrier between steps)."""
+    launch (k = steps, CTAs meeting on a grid barrier between steps); and one-bit
+    grids under Conway's rule on the bit-sliced kernel, one launch per step
+    against 8 steps per launch (temporal blocking)."""
     out = {"workload": f"{steps} steps of one grid, scaled rule r=4 C2 M1, fp8"}
     for n in (512, 1024, 2048):
         init = torch.from_numpy(inputs.bernoulli(n, n, 0.5, SEED + n)).cuda()
@@ -470,6 +472,19 @@ def measure_multistep(torch, cat, inputs, stream, steps=64):
             t = time_launches(torch, lambda: g.step(steps, stream), 3, stream)
             assert g.status() == cat.CAT_OK
             out[f"{n}x{n}_k{k}_cell_updates_per_s"] = n * n * steps / (statistics.median(t) / 1000.0)
+            g.close()
+    # temporal blocking of the bit-sliced kernel on one-bit grids, Conway's rule
+    # (r = 1): one launch per step against 8 steps per launch on tiles kept in
+    # shared memory
+    for n in (512, 2048, 16384):
+        init = torch.from_numpy(inputs.bernoulli(n, n, 0.5, SEED + n)).cuda()
+        for k in (1, 8):
+            g = cat.Grid(n, n, inputs.CONWAY, kernel="bitslice", storage=cat.STORE_BIT1, steps_per_launch=k)
+            g.set_state(init)
+            g.step(steps, stream)
+            t = time_launches(torch, lambda: g.step(steps, stream), 3, stream)
+            assert g.status() == cat.CAT_OK
+            out[f"bits_conway_{n}x{n}_k{k}_cell_updates_per_s"] = n * n * steps / (statistics.median(t) / 1000.0)
             g.close()
     return out
 

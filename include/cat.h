@@ -166,7 +166,7 @@ typedef struct cat_instance *cat_handle_t;
  * instance owns its buffers; cat_destroy frees them.  Uses the current CUDA
  * device.  The kernel defaults to TCGEN05 with FP8 operands; r > 16 with C > 2
  * selects MMA_SYNC with FP16 operands, the simplified von Neumann cross with
- * C > 2 or r > 16 the STENCIL, and one-bit storage with r <= 3 BITSLICE
+ * C > 2 or r > 16 the STENCIL, and one-bit storage with r <= 5 BITSLICE
  * (cat_set_options changes them).  Errors:
  * INVALID_ARG (H or W < 1, H or W > 2^31 - 256, H * pitch > 2^40, bad rule,
  * unknown boundary), UNSUPPORTED (r > 16 with a periodic boundary), OOM,
@@ -194,7 +194,11 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * cooperative launch (all CTAs resident, one per SM) whose CTAs meet on a
  * grid-wide barrier between steps, so small grids stop paying a launch per
  * step; served by TCGEN05 for the Moore neighbourhood with the zero boundary
- * (any dtype, storage or C).  A launch that gives up on a barrier wait sets
+ * (any dtype and C; uint8 or one-bit storage).  With BITSLICE, k steps per
+ * launch with k r <= 8 run as temporal blocking: each block keeps its tile
+ * and a k r-row, k r-cell stale halo in shared memory and advances it k steps
+ * before writing it back (small grids then pay one launch per k steps).  A
+ * tcgen05 launch that gives up on a barrier wait sets
  * the status word like any other bounded wait; cat_status then also resets
  * the barrier counter.  Errors: INVALID_ARG for unknown values,
  * UNSUPPORTED for combinations this build does not serve (e.g. TCGEN05 +

@@ -264,7 +264,9 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.rule = h->rd;
     p.sums = sums;
     p.sums_ld = sums_ld;
-    if (h->kernel == CAT_KERNEL_BITSLICE)
+    if (h->kernel == CAT_KERNEL_BITSLICE && n_steps > 1)   // temporal blocking: n_steps in one launch
+      e = cat::swar_tb_launch(h->buf[in], h->buf[1 - in], h->pitch, h->H, h->W, h->rd, n_steps, s);
+    else if (h->kernel == CAT_KERNEL_BITSLICE)
       e = cat::swar_launch(h->buf[in], h->buf[1 - in], h->pitch, h->H, h->W, h->rd, sums, sums_ld, s);
     else if (h->kernel == CAT_KERNEL_RUNSUM)
       e = cat::runsum_launch(p, s);
@@ -276,30 +278,21 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
 }
 
 // ---------------------------------------------------------------- batches
-// A batch plan: the per-instance descriptor tables and tile work-lists of one
-// handle list, kept on the device, plus cached CUDA graphs of n launches.
-// The instances the short-window kernel serves (FP8, C = 2, r <= 7) form one
-// part and the others a second; each part is one persistent launch per step,
-// the two run side by side on disjoint sets of SMs (their CTAs fill one SM
-// each), sized by their tiles' share of the work.
-struct PlanPart {
-  std::vector<int> idx;       // instances of this part (indices into hs)
-  bool sw = false, encode = false;
+// A batch plan: the per-instance descriptor table and the tile work-list of
+// one handle list, kept on the device, plus cached CUDA graphs of n launches.
+struct BatchPlan {
+  std::vector<cat_instance *> hs;
+  std::vector<int> cur0;      // each instance's current buffer when the table was built
+  int64_t steps_done = 0;     // steps advanced through this plan since then
+  int32_t dtype = 0;
+  bool encode = false;
+  bool sw = false;            // every instance qualifies for the short-window kernel
   cat::BatchInst *d_inst = nullptr;
   cat::BatchTile *d_tiles = nullptr;
   int n_tiles = 0, grid = 0;
-};
-
-struct BatchPlan {
-  std::vector<cat_instance *> hs;
-  std::vector<int> cur0;      // each instance's current buffer when the tables were built
-  int64_t steps_done = 0;     // steps advanced through this plan since then
-  int32_t dtype = 0;
-  PlanPart part[2];           // short-window instances, the others
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // by start parity
   int64_t exec_steps[2] = {0, 0};
-  cudaStream_t capture_stream = nullptr, side_stream = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t capture_stream = nullptr;
 };
 
 std::mutex g_plan_mu;
@@ -309,13 +302,8 @@ void free_plan(BatchPlan *pl) {
   for (int i = 0; i < 2; ++i)
     if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
   if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
-  if (pl->side_stream) cudaStreamDestroy(pl->side_stream);
-  if (pl->fork) cudaEventDestroy(pl->fork);
-  if (pl->join) cudaEventDestroy(pl->join);
-  for (PlanPart &pt : pl->part) {
-    cudaFree(pt.d_inst);
-    cudaFree(pt.d_tiles);
-  }
+  cudaFree(pl->d_inst);
+  cudaFree(pl->d_tiles);
   delete pl;
 }
 
@@ -331,30 +319,27 @@ void drop_plans_with(cat_instance *h) {
   }
 }
 
-// (Re)writes the instance tables of a plan from the handles' current state.
+// (Re)writes the instance table of a plan from the handles' current state.
 int upload_instances(BatchPlan *pl) {
-  CAT_CUDA(cudaDeviceSynchronize());  // earlier launches of this plan may still read the tables
+  CAT_CUDA(cudaDeviceSynchronize());  // earlier launches of this plan may still read the table
+  std::vector<cat::BatchInst> inst(pl->hs.size());
+  memset(inst.data(), 0, inst.size() * sizeof(cat::BatchInst));
   pl->cur0.resize(pl->hs.size());
-  for (PlanPart &pt : pl->part) {
-    if (pt.idx.empty()) continue;
-    std::vector<cat::BatchInst> inst(pt.idx.size());
-    memset(inst.data(), 0, inst.size() * sizeof(cat::BatchInst));
-    for (size_t k = 0; k < pt.idx.size(); ++k) {
-      const cat_instance *h = pl->hs[pt.idx[k]];
-      for (int b = 0; b < 2; ++b) {
-        inst[k].map_in_a[b] = h->maps[b][pt.sw ? 3 : 0];
-        inst[k].map_in_b[b] = h->maps[b][pt.sw ? 4 : 1];
-        inst[k].map_out[b] = h->maps[b][2];
-      }
-      inst[k].rule = h->rd;
-      inst[k].H = (int32_t)h->H;
-      inst[k].W = (int32_t)h->W;
-      inst[k].cur = h->cur;
-      inst[k].err = h->d_err;
-      pl->cur0[pt.idx[k]] = h->cur;
+  for (size_t i = 0; i < pl->hs.size(); ++i) {
+    const cat_instance *h = pl->hs[i];
+    for (int b = 0; b < 2; ++b) {
+      inst[i].map_in_a[b] = h->maps[b][pl->sw ? 3 : 0];
+      inst[i].map_in_b[b] = h->maps[b][pl->sw ? 4 : 1];
+      inst[i].map_out[b] = h->maps[b][2];
     }
-    CAT_CUDA(cudaMemcpy(pt.d_inst, inst.data(), inst.size() * sizeof(cat::BatchInst), cudaMemcpyHostToDevice));
+    inst[i].rule = h->rd;
+    inst[i].H = (int32_t)h->H;
+    inst[i].W = (int32_t)h->W;
+    inst[i].cur = h->cur;
+    inst[i].err = h->d_err;
+    pl->cur0[i] = h->cur;
   }
+  CAT_CUDA(cudaMemcpy(pl->d_inst, inst.data(), inst.size() * sizeof(cat::BatchInst), cudaMemcpyHostToDevice));
   pl->steps_done = 0;
   for (int i = 0; i < 2; ++i) {
     if (pl->exec[i]) cudaGraphExecDestroy(pl->exec[i]);
@@ -369,47 +354,28 @@ int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
   if (!pl) return fail(CAT_ERR_OOM, "host allocation failed");
   pl->hs.assign(hs, hs + count);
   pl->dtype = hs[0]->dtype;
-  // part 0: the short-window instances; part 1: the others.  Work-lists are
-  // ordered by radius (the kernel rebuilds its bands when r changes), tiles
-  // row-major within an instance.
+  pl->encode = false;
+  for (int32_t i = 0; i < count; ++i) pl->encode |= hs[i]->rule.C > 2;
+  pl->sw = true;
+  for (int32_t i = 0; i < count; ++i) pl->sw &= short_window(hs[i]);
+  // work-list: instances ordered by radius, tiles row-major within an instance
   std::vector<int> order(count);
   for (int32_t i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->rule.r < hs[b]->rule.r; });
-  for (int i : order) pl->part[short_window(hs[i]) ? 0 : 1].idx.push_back(i);
-  pl->part[0].sw = true;
-  std::vector<cat::BatchTile> tiles[2];
-  for (int k = 0; k < 2; ++k) {
-    PlanPart &pt = pl->part[k];
-    for (size_t j = 0; j < pt.idx.size(); ++j) {
-      const cat_instance *h = hs[pt.idx[j]];
-      pt.encode |= h->rule.C > 2;
-      const int64_t ty = (h->H + 127) / 128, tx = (h->W + 127) / 128;
-      for (int64_t y = 0; y < ty; ++y)
-        for (int64_t x = 0; x < tx; ++x) tiles[k].push_back(cat::BatchTile{(int32_t)j, (int16_t)y, (int16_t)x});
-    }
-    if (tiles[k].size() > (size_t)INT32_MAX) { delete pl; return fail(CAT_ERR_UNSUPPORTED, "batch too large"); }
-    pt.n_tiles = (int)tiles[k].size();
+  std::vector<cat::BatchTile> tiles;
+  for (int i : order) {
+    const int64_t ty = (hs[i]->H + 127) / 128, tx = (hs[i]->W + 127) / 128;
+    for (int64_t y = 0; y < ty; ++y)
+      for (int64_t x = 0; x < tx; ++x) tiles.push_back(cat::BatchTile{i, (int16_t)y, (int16_t)x});
   }
-  // SMs by work: a short-window tile costs about 0.8 of a standard one
-  const int sms = hs[0]->dev.sms;
-  const double w0 = 0.8 * pl->part[0].n_tiles, w1 = pl->part[1].n_tiles;
-  int g0 = pl->part[1].n_tiles == 0 ? sms : pl->part[0].n_tiles == 0 ? 0 : (int)(sms * w0 / (w0 + w1) + 0.5);
-  g0 = std::max(pl->part[0].n_tiles ? 1 : 0, std::min(g0, sms - (pl->part[1].n_tiles ? 1 : 0)));
-  pl->part[0].grid = std::min(pl->part[0].n_tiles, g0);
-  pl->part[1].grid = std::min(pl->part[1].n_tiles, sms - g0);
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    PlanPart &pt = pl->part[k];
-    if (pt.idx.empty()) continue;
-    e = cudaMalloc(&pt.d_inst, sizeof(cat::BatchInst) * pt.idx.size());
-    if (e == cudaSuccess) e = cudaMalloc(&pt.d_tiles, sizeof(cat::BatchTile) * tiles[k].size());
-    if (e == cudaSuccess)
-      e = cudaMemcpy(pt.d_tiles, tiles[k].data(), sizeof(cat::BatchTile) * tiles[k].size(), cudaMemcpyHostToDevice);
-  }
+  if (tiles.size() > (size_t)INT32_MAX) { delete pl; return fail(CAT_ERR_UNSUPPORTED, "batch too large"); }
+  pl->n_tiles = (int)tiles.size();
+  pl->grid = std::min(pl->n_tiles, hs[0]->dev.sms);
+  cudaError_t e = cudaMalloc(&pl->d_inst, sizeof(cat::BatchInst) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_tiles, sizeof(cat::BatchTile) * tiles.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_tiles, tiles.data(), sizeof(cat::BatchTile) * tiles.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming);
   if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "batch plan"); }
   int rc = upload_instances(pl);
   if (rc) { free_plan(pl); return rc; }
@@ -417,34 +383,17 @@ int build_plan(const cat_handle_t *hs, int32_t count, BatchPlan **out) {
   return CAT_OK;
 }
 
-// n_steps steps of every instance: each part's launches in order on its own
-// stream (part 0 on `s`, part 1 on a side stream forked from and joined back
-// into `s`); the parts share no grid, so they need not meet between steps.
 int launch_batch_steps(BatchPlan *pl, int64_t n_steps, int64_t start, cudaStream_t s) {
-  const bool both = !pl->part[0].idx.empty() && !pl->part[1].idx.empty();
-  if (both) {
-    CAT_CUDA(cudaEventRecord(pl->fork, s));
-    CAT_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->fork, 0));
-  }
-  for (int k = 0; k < 2; ++k) {
-    const PlanPart &pt = pl->part[k];
-    if (pt.idx.empty()) continue;
-    const cudaStream_t ps = (both && k == 1) ? pl->side_stream : s;
-    cat::TcParams p;
-    memset(&p, 0, sizeof(p));
-    p.n_tiles = pt.n_tiles;
-    p.timeout_ns = pl->hs[0]->timeout_ns;
-    p.binst = pt.d_inst;
-    p.btiles = pt.d_tiles;
-    for (int64_t t = 0; t < n_steps; ++t) {
-      p.parity = (int32_t)((start + t) & 1);
-      cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pt.encode, pt.sw, pt.grid, ps);
-      if (e != cudaSuccess) return cuda_fail(e, "batched launch");
-    }
-  }
-  if (both) {
-    CAT_CUDA(cudaEventRecord(pl->join, pl->side_stream));
-    CAT_CUDA(cudaStreamWaitEvent(s, pl->join, 0));
+  cat::TcParams p;
+  memset(&p, 0, sizeof(p));
+  p.n_tiles = pl->n_tiles;
+  p.timeout_ns = pl->hs[0]->timeout_ns;
+  p.binst = pl->d_inst;
+  p.btiles = pl->d_tiles;
+  for (int64_t t = 0; t < n_steps; ++t) {
+    p.parity = (int32_t)((start + t) & 1);
+    cudaError_t e = cat::tc_launch_batch(p, pl->dtype, pl->encode, pl->sw, pl->grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   }
   return CAT_OK;
 }
@@ -630,7 +579,7 @@ int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t boundary
   } else if (rule->r > 16 && rule->C > 2) {  // the paper's fragment scheme with two halo fragments
     h->kernel = CAT_KERNEL_MMA_SYNC;
     h->dtype = CAT_DTYPE_FP16;
-  } else if (storage == CAT_STORE_BIT1 && rule->r <= 3) {  // packed cells at small r: bit planes on CUDA cores
+  } else if (storage == CAT_STORE_BIT1 && rule->r <= 5) {  // packed cells at small r: bit planes on CUDA cores
     h->kernel = CAT_KERNEL_BITSLICE;
     h->dtype = CAT_DTYPE_AUTO;
   }   // r > 16 with C = 2: the tcgen05 wide tile
@@ -669,7 +618,7 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
     cat::InstanceInfo f{};
     cat::host_instance_info(h, &f);
     int32_t k = 0, d = 0, t = 0, w = 0, spl = 0;
-    if (cat::tune_cache_lookup_env(f, &k, &d, &t, &w, &spl) && k >= CAT_KERNEL_TCGEN05 && k <= CAT_KERNEL_BITSLICE &&
+    if (cat::tune_cache_lookup_env(f, &k, &d, &t, &w, &spl) && k >= CAT_KERNEL_TCGEN05 && k <= CAT_KERNEL_RUNSUM &&
         d >= CAT_DTYPE_AUTO && d <= CAT_DTYPE_FP4_E2M1 && spl >= 1) {
       kernel = k;
       dtype = d;
@@ -681,7 +630,7 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_AUTO)
     kernel = vn && (h->rule.C > 2 || wide)                                ? CAT_KERNEL_STENCIL
            : wide && h->rule.C > 2                                        ? CAT_KERNEL_MMA_SYNC
-           : storage == CAT_STORE_BIT1 && h->rule.r <= 3 && h->rule.C == 2 ? CAT_KERNEL_BITSLICE
+           : storage == CAT_STORE_BIT1 && h->rule.r <= 5 && h->rule.C == 2 ? CAT_KERNEL_BITSLICE
                                                                           : CAT_KERNEL_TCGEN05;
   const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
@@ -733,7 +682,11 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
       return fail(CAT_ERR_UNSUPPORTED, "four-bit storage is served by the tcgen05 kernel with FP8 operands, "
                                        "one step per launch");
   }
-  if (steps_per_launch > 1 && (kernel != CAT_KERNEL_TCGEN05 || vn || h->ghost))
+  if (steps_per_launch > 1 && kernel == CAT_KERNEL_BITSLICE) {
+    if ((int64_t)steps_per_launch * h->rule.r > 8 || h->H > 65535ll * 32)
+      return fail(CAT_ERR_UNSUPPORTED, "the bit-sliced kernel runs k steps per launch for k r <= 8 "
+                                       "(and at most 2097120 rows)");
+  } else if (steps_per_launch > 1 && (kernel != CAT_KERNEL_TCGEN05 || vn || h->ghost))
     return fail(CAT_ERR_UNSUPPORTED, "several steps per launch are served by the tcgen05 Moore kernel with the zero boundary");
   if (storage != h->storage && !h->owns_buffers)
     return fail(CAT_ERR_UNSUPPORTED, "an instance on bound buffers keeps uint8 storage");
@@ -826,7 +779,9 @@ int cat_step(cat_handle_t h, int64_t n_steps, void *stream) {
     const int m = (int)std::min<int64_t>(h->steps_per_launch, n_steps - t);
     int rc = launch_step(h, h->cur, nullptr, 0, (cudaStream_t)stream, m);
     if (rc) return rc;
-    h->cur ^= m & 1;
+    // the tcgen05 multi-step launch alternates buffers step by step; the
+    // blocked bit-sliced launch writes its last step to the other buffer
+    h->cur ^= h->kernel == CAT_KERNEL_BITSLICE ? 1 : (m & 1);
     t += m;
   }
   return CAT_OK;

@@ -149,9 +149,14 @@ cudaError_t mma_launch(const SimpleParams &p, int dt, cudaStream_t s);
 // (cat_stencil.cu).
 cudaError_t stencil_launch(const SimpleParams &p, cudaStream_t s);
 cudaError_t runsum_launch(const SimpleParams &p, cudaStream_t s);
-// Bit-sliced CUDA-core step on one-bit storage, r <= 3 (cat_swar.cu): in/out
+// Bit-sliced CUDA-core step on one-bit storage, r <= 5 (cat_swar.cu): in/out
 // are packed rows at `pitch` bytes (a multiple of 4); sums: counts instead.
 cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
                         int32_t *sums, int64_t sums_ld, cudaStream_t s);
+// The same rule, k steps per launch on tiles held in shared memory (temporal
+// blocking, a k r-cell stale halo; k r <= 8); reads `in`, writes the state
+// after k steps to `out`.
+cudaError_t swar_tb_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
+                           int k, cudaStream_t s);
 
 }  // namespace cat

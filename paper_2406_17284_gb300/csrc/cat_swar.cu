@@ -192,7 +192,127 @@ __global__ void __launch_bounds__(kBlock) ltl_swar_kernel(const SwarParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Temporal blocking: k steps per launch on a tile kept in shared memory.  A
+// block holds 128 word columns (the 126 of its tile and one on each side) of
+// rows y0 - kR .. y0 + 32 + kR - 1; step s computes the rows whose 2R + 1-row
+// neighbourhood is still valid after s - 1 steps (the stale halo grows by R
+// rows, and R cells into the side words, per step), from one buffer into the
+// other, and after k steps the tile's 32 x 126 words are written out.  Cells
+// outside the grid are forced back to 0 after every step.  k R <= 8: two
+// buffers of 48 rows x 128 words (48 KiB of dynamic shared memory).
+constexpr int kTbThreads = 128, kTbTile = kTbThreads - 2, kTbRows = 32, kTbMaxHalo = 8;
+constexpr int kTbBufRows = kTbRows + 2 * kTbMaxHalo;
+constexpr int kTbSmem = 2 * kTbBufRows * kTbThreads * 4;
+
+template <int R>
+__global__ void __launch_bounds__(kTbThreads) ltl_swar_tb_kernel(const SwarParams p, int k) {
+  constexpr int NH = Bits<R>::kH, NS = Bits<R>::kS, WIN = 2 * R + 1;
+  extern __shared__ uint32_t tb_smem[];
+  uint32_t(*buf)[kTbBufRows][kTbThreads] = reinterpret_cast<uint32_t(*)[kTbBufRows][kTbThreads]>(tb_smem);
+  const int c = threadIdx.x;                                   // column in the block
+  const int wi = blockIdx.x * kTbTile - 1 + c;                 // word column in the grid
+  const int halo = k * R, rows = kTbRows + 2 * halo;
+  const int64_t y0 = (int64_t)blockIdx.y * kTbRows;
+  const int last_bits = p.W - 32 * (p.words - 1);
+  const bool col = wi >= 0 && wi < p.words;
+  const uint32_t mask = !col ? 0u : (wi == p.words - 1 && last_bits < 32) ? (1u << last_bits) - 1u : ~0u;
+  const RangeBits<NS> surv = range_bits<NS>(p.rule.s_lo, p.rule.s_w), born = range_bits<NS>(p.rule.b_lo, p.rule.b_w);
+  for (int i = 0; i < rows; ++i) {
+    const int64_t y = y0 - halo + i;
+    buf[0][i][c] = (col && y >= 0 && y < p.H) ? __ldg(p.in + y * p.pitch_words + wi) & mask : 0u;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int s = 1; s <= k; ++s) {
+    const uint32_t(*A)[kTbThreads] = buf[cur];
+    uint32_t(*B)[kTbThreads] = buf[cur ^ 1];
+    auto hsum = [&](int i, uint32_t (&h)[NH], uint32_t &centre) {
+      const uint32_t w = A[i][c];
+      const uint32_t left = c > 0 ? A[i][c - 1] : 0u, right = c < kTbThreads - 1 ? A[i][c + 1] : 0u;
+#pragma unroll
+      for (int b = 0; b < NH; ++b) h[b] = 0u;
+      const uint32_t w1[1] = {w};
+      bs_add<NH, 1>(h, w1);
+#pragma unroll
+      for (int d = 1; d <= R; ++d) {
+        const uint32_t l[1] = {__funnelshift_l(left, w, d)};
+        const uint32_t r[1] = {__funnelshift_r(w, right, d)};
+        bs_add<NH, 1>(h, l);
+        bs_add<NH, 1>(h, r);
+      }
+      centre = w;
+    };
+    // rows lo .. hi - 1 of the buffer are computed in this step
+    const int lo = s * R, hi = rows - s * R;
+    uint32_t hs[WIN][NH], cs[WIN];
+#pragma unroll
+    for (int q = 0; q < WIN - 1; ++q) hsum(lo - R + q, hs[q + 1], cs[q + 1]);
+    for (int i = lo; i < hi; ++i) {
+#pragma unroll
+      for (int q = 0; q < WIN - 1; ++q) {
+#pragma unroll
+        for (int b = 0; b < NH; ++b) hs[q][b] = hs[q + 1][b];
+        cs[q] = cs[q + 1];
+      }
+      hsum(i + R, hs[WIN - 1], cs[WIN - 1]);
+      uint32_t S[NS];
+#pragma unroll
+      for (int b = 0; b < NS; ++b) S[b] = b < NH ? hs[0][b] : 0u;
+#pragma unroll
+      for (int q = 1; q < WIN; ++q) bs_add<NS, NH>(S, hs[q]);
+      const int64_t y = y0 - halo + i;
+      const uint32_t cc = cs[R];
+      const uint32_t nxt = (cc & bs_in<NS>(S, surv)) | (~cc & bs_in<NS>(S, born));
+      B[i][c] = (y >= 0 && y < p.H) ? nxt & mask : 0u;   // cells outside the grid stay dead
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (c == 0 || c == kTbThreads - 1 || !col) return;
+  for (int i = 0; i < kTbRows; ++i) {
+    const int64_t y = y0 + i;
+    if (y >= p.H) break;
+    p.out[y * p.pitch_words + wi] = buf[cur][halo + i][c];
+  }
+}
+
 }  // namespace
+
+cudaError_t swar_tb_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
+                           int k, cudaStream_t s) {
+  if (k < 1 || k * rule.r > kTbMaxHalo) return cudaErrorInvalidValue;
+  SwarParams p;
+  p.in = reinterpret_cast<const uint32_t *>(in);
+  p.out = reinterpret_cast<uint32_t *>(out);
+  p.pitch_words = pitch / 4;
+  p.H = (int32_t)H;
+  p.W = (int32_t)W;
+  p.words = (int32_t)((W + 31) / 32);
+  p.rule = rule;
+  p.sums = nullptr;
+  p.sums_ld = 0;
+  const int64_t strips = (H + kTbRows - 1) / kTbRows;
+  if (strips > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((p.words + kTbTile - 1) / kTbTile), (unsigned)strips);
+  void (*kern)(SwarParams, int) = nullptr;
+  switch (rule.r) {
+    case 1: kern = ltl_swar_tb_kernel<1>; break;
+    case 2: kern = ltl_swar_tb_kernel<2>; break;
+    case 3: kern = ltl_swar_tb_kernel<3>; break;
+    case 4: kern = ltl_swar_tb_kernel<4>; break;
+    case 5: kern = ltl_swar_tb_kernel<5>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  static bool configured[6] = {false, false, false, false, false, false};
+  if (!configured[rule.r]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTbSmem);
+    if (e != cudaSuccess) return e;
+    configured[rule.r] = true;
+  }
+  kern<<<grid, kTbThreads, kTbSmem, s>>>(p, k);
+  return cudaGetLastError();
+}
 
 cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
                         int32_t *sums, int64_t sums_ld, cudaStream_t s) {

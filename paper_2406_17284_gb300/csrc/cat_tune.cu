@@ -98,7 +98,7 @@ std::vector<Cand> candidates(const InstanceInfo &f) {
   out.push_back({CAT_KERNEL_MMA_SYNC, CAT_DTYPE_INT8, 0, 0, 1});
   out.push_back({CAT_KERNEL_STENCIL, CAT_DTYPE_AUTO, 0, 0, 1});
   out.push_back({CAT_KERNEL_RUNSUM, CAT_DTYPE_AUTO, 0, 0, 1});
-  out.push_back({CAT_KERNEL_BITSLICE, CAT_DTYPE_AUTO, 0, 0, 1});
+  for (int spl : {1, 2, 4, 8}) out.push_back({CAT_KERNEL_BITSLICE, CAT_DTYPE_AUTO, 0, 0, spl});
   return out;
 }
 

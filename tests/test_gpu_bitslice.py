@@ -152,3 +152,36 @@ def test_unsupported(cat):
         with pytest.raises(cat.CatError) as e:
             cat.Grid(64, 64, rule, kernel="bitslice", **kw)
         assert e.value.code == cat.CAT_ERR_UNSUPPORTED, (rule, kw)
+
+
+@pytest.mark.parametrize("r,k", [(1, 2), (1, 3), (1, 8), (2, 4), (4, 2), (5, 1)])
+def test_temporal_blocking_vs_oracle(cat, r, k):
+    """k steps per launch on tiles kept in shared memory (a k r-cell stale
+    halo): shapes that cross block tiles (126 words = 4032 cells wide, 32 rows
+    high) and grid edges, step counts that do and do not divide by k."""
+    rule = inputs.scaled_rule(r, M=r % 2)
+    for i, (H, W) in enumerate([(200, 4100), (33, 8100), (70, 31), (1, 300), (129, 4032)]):
+        grid = inputs.bernoulli(H, W, 0.5, 900 + 10 * r + i)
+        g = cat.Grid(H, W, rule, kernel="bitslice", storage=cat.STORE_BIT1, steps_per_launch=k)
+        try:
+            g.set_state(grid)
+            g.step(2 * k + 1)
+            assert g.status() == cat.CAT_OK
+            assert_same(g.get_state(), oracle.step(grid, orule(rule), n_steps=2 * k + 1), f"{H}x{W} r={r} k={k}")
+            assert not np.unpackbits(g.state_tensor().cpu().numpy(), axis=1, bitorder="little")[:, W:].any()
+        finally:
+            g.close()
+
+
+def test_temporal_blocking_conway_and_limits(cat):
+    grid = inputs.bernoulli(1024, 1024, 0.5, 77)
+    g = cat.Grid(1024, 1024, inputs.CONWAY, kernel="bitslice", storage=cat.STORE_BIT1, steps_per_launch=8)
+    try:
+        g.set_state(grid)
+        g.step(100)
+        assert_same(g.get_state(), oracle.step(grid, orule(inputs.CONWAY), n_steps=100), "Conway 100, k = 8")
+    finally:
+        g.close()
+    with pytest.raises(cat.CatError) as e:
+        cat.Grid(64, 64, inputs.scaled_rule(3), kernel="bitslice", storage=cat.STORE_BIT1, steps_per_launch=3)
+    assert e.value.code == cat.CAT_ERR_UNSUPPORTED      # k r = 9 > 8
