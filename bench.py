@@ -731,8 +731,13 @@ def run_cat(args, rank, world, local):
             multistate["single_nib4_cell_updates_per_s"], 1.0, e4m3_peak, hbm)
     roofs(periodic, [k for k in (periodic or {}) if k.endswith("_per_s")], 2.0, e4m3_peak)
     roofs(bits, ["cell_updates_per_s"], 0.25, e4m3_peak)
+    if bits and bits.get("bitslice_cell_updates_per_s"):   # CUDA cores: the one-bit HBM term
+        bits["bitslice_roofline"] = {r: roof(v, 0.25, None, hbm) for r, v in bits["bitslice_cell_updates_per_s"].items()}
     roofs(vn, ["cell_updates_per_s"], 2.0, e4m3_peak)
-    roofs(multistep, [k for k in (multistep or {}) if k.endswith("_per_s")], 2.0, e4m3_peak)
+    roofs(multistep, [k for k in (multistep or {}) if k.endswith("_per_s") and not k.startswith("bits_")], 2.0, e4m3_peak)
+    if multistep:
+        multistep["roofline"].update({k: roof(v, 0.25, None, hbm) for k, v in multistep.items()
+                                      if k.startswith("bits_") and k.endswith("_per_s")})
     roofs(wide, [k for k in (wide or {}) if k.endswith("_per_s")], 2.0, None)
     comp_roofs = {}
     for k, row in comps.items():
