@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-vn", action="store_true", help="skip the simplified von Neumann measurement")
     ap.add_argument("--no-multistep", action="store_true", help="skip the several-steps-per-launch measurement")
     ap.add_argument("--no-wide", action="store_true", help="skip the r > 16 measurement")
+    ap.add_argument("--no-fp4", action="store_true", help="skip the FP4 / FP8 precision measurement")
     return ap.parse_args()
 
 
@@ -176,7 +177,7 @@ def measure_tensor_peaks(torch, cat, stream):
     sms = torch.cuda.get_device_properties(stream.device).multi_processor_count
     status = torch.zeros(1, dtype=torch.int32, device=stream.device)
     out = {}
-    for name, dt, K in (("e4m3", cat.DTYPE_FP8_E4M3, 32), ("f16", cat.DTYPE_FP16, 16)):
+    for name, dt, K in (("e4m3", cat.DTYPE_FP8_E4M3, 32), ("e2m1", cat.DTYPE_FP4_E2M1, 32), ("f16", cat.DTYPE_FP16, 16)):
         def flops(n):
             return sms * n * 2.0 * 128 * 256 * K
         n_burst, n_sus = 1 << 15, 1 << 23
@@ -190,7 +191,7 @@ def measure_tensor_peaks(torch, cat, stream):
         if int(status.item()) != 0:
             raise RuntimeError(f"tensor probe ({name}) timed out")
         out[name] = {"burst_tflops": burst, "sustained_tflops": sustained}
-    out["how"] = ("cat_tensor_probe: one CTA per SM, one thread issuing tcgen05.mma M=128 N=256 (K=32 e4m3 "
+    out["how"] = ("cat_tensor_probe: one CTA per SM, one thread issuing tcgen05.mma M=128 N=256 (K=32 e4m3 or e2m1 "
                   "kind::f8f6f4 / K=16 f16 kind::f16), f32 accumulators; burst = median of 10 launches of "
                   "2^15 MMAs per SM, sustained = one launch of 2^23")
     return out
@@ -540,6 +541,35 @@ def measure_bits(args, torch, cat, inputs, stream, d_init, hbm):
             "traffic_bytes_per_launch": recorded_traffic("bits", n * n), "kernel": "ltl_bits_kernel"}
 
 
+PREC_N, PREC_P, PREC_RADII = 32768, 0.35, (1, 5, 10, 16)
+
+
+def measure_fp4(args, torch, cat, inputs, stream):
+    """Operand precisions on tcgen05 at the precision workload's size (32768^2,
+    Bernoulli(0.35), the scaled rule C2 M1, r in {1, 5, 10, 16}): FP4 (e2m1
+    pass-1 operands, e4m3 digits in pass 2) and FP8 (e4m3) on uint8, one-bit and
+    four-bit storage, the median of five launches per grid."""
+    n = PREC_N if args.size == N else args.size
+    init = torch.from_numpy(inputs.bernoulli(n, n, PREC_P, SEED + 3)).to(stream.device)
+    out = {"workload": f"{n}x{n} bernoulli{PREC_P}, scaled rule C2 M1, r in {list(PREC_RADII)}",
+           "bytes_per_cell": {"u8": 2.0, "bit1": 0.25, "nib4": 1.0}}
+    for st_name, st in (("u8", cat.STORE_U8), ("bit1", cat.STORE_BIT1), ("nib4", cat.STORE_NIB4)):
+        for dt in ("fp4", "fp8"):
+            row = {}
+            for r in PREC_RADII:
+                g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel="tcgen05", dtype=dt, storage=st)
+                g.set_state(init)
+                g.step(2, stream)
+                t = time_launches(torch, lambda: g.step(1, stream), 5, stream)
+                assert g.status() == cat.CAT_OK
+                row[str(r)] = n * n / (statistics.median(t) / 1000.0)
+                g.close()
+            out[f"{dt}_{st_name}_cell_updates_per_s"] = row
+    del init
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_cat(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -704,6 +734,9 @@ def run_cat(args, rank, world, local):
     wide = None
     if not args.no_wide and rank == 0:
         wide = measure_wide(args, torch, cat, inputs, stream, d_init)
+    fp4 = None
+    if not args.no_fp4 and rank == 0:
+        fp4 = measure_fp4(args, torch, cat, inputs, stream)
 
     cpu = None
     if rank == 0:
@@ -739,6 +772,12 @@ def run_cat(args, rank, world, local):
         multistep["roofline"].update({k: roof(v, 0.25, None, hbm) for k, v in multistep.items()
                                       if k.startswith("bits_") and k.endswith("_per_s")})
     roofs(wide, [k for k in (wide or {}) if k.endswith("_per_s")], 2.0, None)
+    if fp4:   # per storage and dtype: that storage's bytes, that operand dtype's tensor rate
+        e2m1_peak = tensor_peaks["e2m1"]["burst_tflops"]
+        fp4["roofline_frac"] = {
+            k: {r: roof(v, fp4["bytes_per_cell"][k.split("_")[1]], e2m1_peak if k.startswith("fp4") else e4m3_peak,
+                        hbm, "e2m1 burst" if k.startswith("fp4") else "e4m3 burst")["frac"] for r, v in row.items()}
+            for k, row in fp4.items() if k.endswith("_per_s")}
     comp_roofs = {}
     for k, row in comps.items():
         tp = f16_peak if k == "tcgen05/fp16" else e4m3_peak if k == "tcgen05/fp8" else None
@@ -783,6 +822,7 @@ def run_cat(args, rank, world, local):
             "von_neumann": vn,
             "multistep": multistep,
             "wide_radius": wide,
+            "precisions": fp4,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
                     "d2h_bytes_per_step": n * n * len(RADII), "host_link": link,
                     "link_bound_cell_updates_per_s": link["bidirectional_gbs_each_way"] * 1e9 * world},

@@ -92,7 +92,14 @@ enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
  *             96 x 96 tile (H <= 65) as two e4m3 digits, H & 15 against the
  *             band and H >> 4 against a band of 16s (f32 accumulation).
  *   INT8      H <= 65 < 127; served by MMA_SYNC (sm_103a has no tcgen05 kind::i8).
- *   FP4_E2M1  not served by this build (UNSUPPORTED).                         */
+ *   FP4_E2M1  TCGEN05, Moore, r <= 16, one step per launch, uint8 / one-bit /
+ *             four-bit storage, any C: the window is re-encoded as e2m1 (a
+ *             state-1 cell 0.5; kind::f8f6f4 reads e2m1 from shared memory as
+ *             16 elements packed into the first 8 bytes of each 16-byte unit)
+ *             against an e2m1 band of ones, so pass 1 gives H / 2 exactly.
+ *             H <= 33 is not an e2m1 number (the largest is 6), so pass 2
+ *             takes H as two e4m3 digits, H & 15 and H - (H & 15), against
+ *             the e4m3 band of ones: the e2m1 / e4m3 mix of kind::f8f6f4. */
 enum {
   CAT_DTYPE_AUTO = 0,
   CAT_DTYPE_FP16 = 1,
@@ -107,7 +114,7 @@ enum {
  *         bit x % 8 of byte x / 8 (lowest x in the lowest bit), so a row takes
  *         ceil(W / 8) bytes and the bits past W in the last byte stay 0.  An
  *         eighth of the HBM traffic of U8.  Stepped by the TCGEN05 kernel on
- *         FP8 operands, or by BITSLICE for r <= 5, with the zero boundary
+ *         FP8 or FP4 operands, or by BITSLICE for r <= 5, with the zero boundary
  *         (Moore neighbourhood); cat_batch_step advances BIT1
  *         instances one launch per instance and step.  The state is still
  *         passed in and out one byte per cell (cat_set_state/cat_get_state
@@ -116,8 +123,8 @@ enum {
  *         of the Generations reading): cell x of a row is nibble x % 2 of
  *         byte x / 2 (even x in the low nibble), so a row takes ceil(W / 2)
  *         bytes and the nibble past an odd W stays 0.  Half the HBM traffic
- *         of U8.  Stepped by the TCGEN05 kernel on FP8 operands (the window
- *         unpacked to state-1 flags in shared memory), r <= 16, Moore, the
+ *         of U8.  Stepped by the TCGEN05 kernel on FP8 or FP4 operands (the
+ *         window unpacked to state-1 flags in shared memory), r <= 16, Moore, the
  *         zero boundary, one step per launch; cat_batch_step advances NIB4
  *         instances one launch per instance and step.  State in and out as
  *         with BIT1.                                                        */
@@ -188,8 +195,9 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * TCGEN05, FP16 for MMA_SYNC; instances start with CAT_STORE_U8).  A change
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).
- * CAT_STORE_BIT1 needs C = 2, the zero boundary and TCGEN05 with FP8_E4M3,
- * or BITSLICE (r <= 5).
+ * CAT_STORE_BIT1 needs C = 2, the zero boundary and TCGEN05 with FP8_E4M3 or
+ * FP4_E2M1, or BITSLICE (r <= 5).  CAT_STORE_NIB4 needs TCGEN05 with
+ * FP8_E4M3 or FP4_E2M1.
  * steps_per_launch = k > 1 makes cat_step run k steps per kernel launch: one
  * cooperative launch (all CTAs resident, one per SM) whose CTAs meet on a
  * grid-wide barrier between steps, so small grids stop paying a launch per
@@ -202,7 +210,8 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
  * the status word like any other bounded wait; cat_status then also resets
  * the barrier counter.  Errors: INVALID_ARG for unknown values,
  * UNSUPPORTED for combinations this build does not serve (e.g. TCGEN05 +
- * INT8: sm_103a has no tcgen05 kind::i8), OOM, CUDA.  After INVALID_ARG,
+ * INT8: sm_103a has no tcgen05 kind::i8; FP4_E2M1 with r > 16, the von
+ * Neumann cross or k > 1), OOM, CUDA.  After INVALID_ARG,
  * UNSUPPORTED or OOM the instance keeps its previous options and state.     */
 CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t storage,
                     int32_t steps_per_launch);
@@ -217,7 +226,7 @@ CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32
  *   window_rows  0: chosen by the rule (144 for FP8 operands, C = 2, r <= 7,
  *            else 160); 144: the short window (128 x 128 tile, FP8, C = 2,
  *            r <= 7, uint8 storage); 160: the full window.
- * The autotuner in the Python package drives this call.  Later changes of
+ * The autotuner (cat_autotune) drives this call.  Later changes of
  * kernel, dtype or storage that a chosen tile does not serve are rejected by
  * cat_set_options.  Errors: INVALID_ARG (other shapes), UNSUPPORTED (a shape
  * the instance's kernel, dtype, storage, boundary or rule does not serve). */
@@ -392,8 +401,9 @@ CAT_API int cat_batch_step_static(const cat_grid_desc_t *grids, int32_t count, i
  * Sec. IV-D, uses the vendor's peak).  Launches one CTA per SM, each issuing
  * mmas_per_sm back-to-back MMAs of M = 128, N = 256 with zero operands in
  * shared memory and f32 accumulators in tensor memory; dtype
- * CAT_DTYPE_FP8_E4M3 (K = 32, kind::f8f6f4) or CAT_DTYPE_FP16 (K = 16,
- * kind::f16).  The caller times the launch on `stream`; it performs
+ * CAT_DTYPE_FP8_E4M3 or CAT_DTYPE_FP4_E2M1 (K = 32, kind::f8f6f4) or
+ * CAT_DTYPE_FP16 (K = 16, kind::f16).  The caller times the launch on
+ * `stream`; it performs
  * SMs x mmas_per_sm x 2 x 128 x 256 x K flops.  d_status (device int32,
  * required) receives a non-zero code if the bounded wait for the MMAs gave
  * up; the caller zeroes it.  Errors: INVALID_ARG (mmas_per_sm outside

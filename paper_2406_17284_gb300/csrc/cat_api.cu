@@ -247,8 +247,10 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     p.timeout_ns = h->timeout_ns;
     p.inject = h->inject;
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
+    const bool fp4 = h->dtype == CAT_DTYPE_FP4_E2M1;
     e = vn ? cat::vn_launch(p, grid, s)
            : wide ? cat::wide_launch(p, grid, s)
+           : fp4  ? cat::fp4_launch(p, bits ? 1 : nib ? 2 : 0, grid, s)
            : nib  ? cat::nib_launch(p, grid, s)
                   : cat::tc_launch(p, h->dtype, bits || h->rule.C > 2, sw, bits, grid, s);
     if (e == cudaSuccess && n_steps > 1) h->gbar_count += (uint32_t)grid * (uint32_t)(n_steps - 1);
@@ -634,9 +636,12 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
                                                                           : CAT_KERNEL_TCGEN05;
   const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
   if (dtype == CAT_DTYPE_AUTO) dtype = kernel == CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP8_E4M3 : CAT_DTYPE_FP16;
-  if (kernel == CAT_KERNEL_TCGEN05 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP8_E4M3)
-    return fail(CAT_ERR_UNSUPPORTED, dtype == CAT_DTYPE_INT8 ? "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC"
-                                                             : "dtype %d is not served by the tcgen05 kernel", dtype);
+  if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_INT8)
+    return fail(CAT_ERR_UNSUPPORTED, "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC");
+  if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_FP4_E2M1 &&
+      (vn || wide || cur_tile == 96 || steps_per_launch > 1))
+    return fail(CAT_ERR_UNSUPPORTED, "FP4 operands are served by the 128 x 128 tcgen05 Moore kernel (r <= 16), "
+                                     "one step per launch");
   if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "the mma.sync kernel serves FP16 and INT8 operands");
   if (kernel == CAT_KERNEL_STENCIL || kernel == CAT_KERNEL_RUNSUM) dtype = CAT_DTYPE_INT8;  // integer counts on CUDA cores
@@ -670,16 +675,16 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (storage == CAT_STORE_BIT1) {
     if (h->rule.C != 2) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage holds two-state rules only");
     if (h->ghost) return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served with the zero boundary only");
-    if ((kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3) && kernel != CAT_KERNEL_BITSLICE)
-      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 operands "
+    if ((kernel != CAT_KERNEL_TCGEN05 || dtype == CAT_DTYPE_FP16) && kernel != CAT_KERNEL_BITSLICE)
+      return fail(CAT_ERR_UNSUPPORTED, "one-bit storage is served by the tcgen05 kernel with FP8 or FP4 operands "
                                        "and by the bit-sliced kernel");
   }
   if (storage == CAT_STORE_NIB4) {
     if (h->rule.C > 16 || h->ghost || vn || wide)
       return fail(CAT_ERR_UNSUPPORTED, "four-bit storage holds rules with C <= 16, r <= 16, the Moore "
                                        "neighbourhood and the zero boundary");
-    if (kernel != CAT_KERNEL_TCGEN05 || dtype != CAT_DTYPE_FP8_E4M3 || steps_per_launch > 1)
-      return fail(CAT_ERR_UNSUPPORTED, "four-bit storage is served by the tcgen05 kernel with FP8 operands, "
+    if (kernel != CAT_KERNEL_TCGEN05 || dtype == CAT_DTYPE_FP16 || steps_per_launch > 1)
+      return fail(CAT_ERR_UNSUPPORTED, "four-bit storage is served by the tcgen05 kernel with FP8 or FP4 operands, "
                                        "one step per launch");
   }
   if (steps_per_launch > 1 && kernel == CAT_KERNEL_BITSLICE) {
@@ -796,10 +801,10 @@ int cat_batch_step(const cat_handle_t *hs, int32_t count, int64_t n_steps, void 
   }
   if (count == 0 || n_steps == 0) return CAT_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  bool all_tc = true;   // Moore, zero boundary, uint8 storage: other instances step one by one
+  bool all_tc = true;   // Moore, zero boundary, uint8 storage, no FP4: other instances step one by one
   for (int32_t i = 0; i < count; ++i) {
     all_tc &= hs[i]->kernel == CAT_KERNEL_TCGEN05 && hs[i]->ghost == 0 && hs[i]->storage == CAT_STORE_U8 &&
-              hs[i]->rule.nbhd == 'M' && !wide_tile(hs[i]);
+              hs[i]->rule.nbhd == 'M' && !wide_tile(hs[i]) && hs[i]->dtype != CAT_DTYPE_FP4_E2M1;
     if (hs[i]->dev.id != hs[0]->dev.id) return fail(CAT_ERR_INVALID_ARG, "instances of a batch must share the device");
   }
   if (all_tc) {   // one persistent launch over every instance: one kernel instantiation

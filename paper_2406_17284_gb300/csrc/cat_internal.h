@@ -95,6 +95,10 @@ cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s);
 // instance): map_in_a / map_in_b the 128 x 160 and 32 x 160 window maps,
 // map_ctr / map_out the 96 x 96 tile maps; tiles_x, n_tiles in 96 x 96 tiles.
 cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s);
+// FP4 (e2m1) pass-1 operands, pass 2 on e4m3 digits, on the re-encoded window
+// of uint8 (storage 0), one-bit (1) or four-bit (2) grids: the maps of the
+// FP8 kernel for that storage.
+cudaError_t fp4_launch(const TcParams &p, int storage, int grid, cudaStream_t s);
 // Four bits per cell (FP8 on a re-encoded window, C <= 16, single instance):
 // map_in_a the 96 x 160-byte window map, map_ctr / map_out the 64 x 128-byte
 // tile maps (64B swizzle) of the packed buffers.

@@ -35,7 +35,8 @@ __device__ __forceinline__ void probe_mma(uint32_t d, uint64_t a, uint64_t b, ui
   else mma_f8f6f4(d, a, b, idesc, acc);
 }
 
-// KIND 0: kind::f16 (f16 operands, K = 16); KIND 1: kind::f8f6f4 (e4m3, K = 32).
+// KIND 0: kind::f16 (f16 operands, K = 16); KIND 1: kind::f8f6f4 (e4m3, K = 32);
+// KIND 2: kind::f8f6f4 with e2m1 operands (K = 32).
 template <int KIND>
 __global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t n_mma, uint64_t timeout_ns, int32_t *err) {
   extern __shared__ uint8_t smem_raw[];
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t n_mma, uint64
     const uint32_t base = smem_u32(smem);
     const uint64_t a = smem_desc(base, 16, 1024, kSwizzle128B);
     const uint64_t b = smem_desc(base + kProbeA, 16, 1024, kSwizzle128B);
-    const uint32_t idesc = idesc_f32acc(128, kProbeN);
+    const uint32_t idesc = idesc_f32acc(128, kProbeN) | (KIND == 2 ? kIdescE2M1 : 0u);
     probe_mma<KIND>(tmem, a, b, idesc, 0);
     int64_t i = 1;
     for (; i + 8 <= n_mma; i += 8) {
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t n_mma, uint64
 }  // namespace cat
 
 extern "C" CAT_API int cat_tensor_probe(int32_t dtype, int64_t mmas_per_sm, int32_t *d_status, void *stream) {
-  if (dtype != CAT_DTYPE_FP8_E4M3 && dtype != CAT_DTYPE_FP16)
-    return cat::host_fail(CAT_ERR_UNSUPPORTED, "the tensor probe measures FP8 e4m3 and FP16 MMAs");
+  if (dtype != CAT_DTYPE_FP8_E4M3 && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_FP4_E2M1)
+    return cat::host_fail(CAT_ERR_UNSUPPORTED, "the tensor probe measures FP8 e4m3, FP4 e2m1 and FP16 MMAs");
   if (mmas_per_sm < 1 || mmas_per_sm > (int64_t)1 << 30)
     return cat::host_fail(CAT_ERR_INVALID_ARG, "mmas_per_sm must be in [1, 2^30]");
   if (!d_status) return cat::host_fail(CAT_ERR_INVALID_ARG, "d_status is NULL");
@@ -103,7 +104,8 @@ extern "C" CAT_API int cat_tensor_probe(int32_t dtype, int64_t mmas_per_sm, int3
   if (major != 10 || minor != 3) return cat::host_fail(CAT_ERR_UNSUPPORTED, "this library is built for sm_103a");
   cudaStream_t s = (cudaStream_t)stream;
   void (*kern)(int64_t, uint64_t, int32_t *) =
-      dtype == CAT_DTYPE_FP16 ? cat::mma_probe_kernel<0> : cat::mma_probe_kernel<1>;
+      dtype == CAT_DTYPE_FP16 ? cat::mma_probe_kernel<0>
+    : dtype == CAT_DTYPE_FP4_E2M1 ? cat::mma_probe_kernel<2> : cat::mma_probe_kernel<1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cat::kProbeDyn);
   // the bounded wait: 1 us per MMA (over ten times its duration) plus 1 s
   const uint64_t timeout_ns = 1000000000ull + (uint64_t)mmas_per_sm * 1000ull;

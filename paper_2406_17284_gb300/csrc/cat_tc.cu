@@ -240,9 +240,28 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, Bars *
   return __all_sync(0xffffffffu, ok);
 }
 
+// One 16-cell unit of the e2m1 window operand (kind::f8f6f4 reads e2m1 from
+// shared memory as 16 elements packed into the first 8 bytes of every 16-byte
+// unit, element 2i in the low nibble of byte i; bytes 8..15 are not read):
+// the flags 0/1 of the 16 cells, bytes of w[0..3], as e2m1 codes 0 / 1 (0.5).
+__device__ __forceinline__ uint2 fp4_unit(const uint32_t (&w)[4]) {
+  // w | w >> 4 holds cells 0, 1 in byte 0 and cells 2, 3 in byte 2
+  return make_uint2(__byte_perm(w[0] | (w[0] >> 4), w[1] | (w[1] >> 4), 0x6420),
+                    __byte_perm(w[2] | (w[2] >> 4), w[3] | (w[3] >> 4), 0x6420));
+}
+
+// Eight cells' bits (bits 0..7 of b) -> eight nibbles 0/1 (bit i to bit 4i).
+__device__ __forceinline__ uint32_t bits8_to_nibbles(uint32_t b) {
+  uint32_t x = b & 0xFFu;
+  x = (x | (x << 12)) & 0x000F000Fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  return (x | (x << 3)) & 0x11111111u;
+}
+
 // Encodes the 160 x 160 u8 window xs as operand values: alive (state 1) ->
-// 0x01 (e4m3 2^-9, FP8 kernel) or f16 1.0 (FP16 kernel), anything else -> 0.
-template <int E>
+// 0x01 (e4m3 2^-9, FP8 kernel), f16 1.0 (FP16 kernel) or e2m1 0.5 (FP4
+// kernel, packed units), anything else -> 0.
+template <int E, bool FP4 = false>
 __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bool multistate,
                                               int tid, int nthr) {
   // consecutive threads take consecutive rows of one 16-byte column chunk, so
@@ -255,7 +274,9 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
 #pragma unroll
       for (int i = 0; i < 4; ++i) w[i] = __vcmpeq4(w[i], 0x01010101u) & 0x01010101u;
     }
-    if constexpr (E == 1) {
+    if constexpr (FP4) {
+      *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * c)) = fp4_unit(w);
+    } else if constexpr (E == 1) {
       *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
       uint32_t h[8];
@@ -275,10 +296,12 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
 __device__ __forceinline__ uint32_t bits4_to_bytes(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
 
 // Unpacks a bit-packed window stage (160 rows of 48 bytes, window cell x' at
-// bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell.
-// One item is half a row (80 cells, 16-cell chunks 5h .. 5h+4): three aligned
-// 32-bit loads (bytes 12 + 12h ..), shifted by 16 bits for h = 0 so that the
-// chunks are the five consecutive 16-bit fields.
+// bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell
+// (FP4: e2m1 units, code 1 for a live cell).  One item is half a row (80
+// cells, 16-cell chunks 5h .. 5h+4): three aligned 32-bit loads (bytes 12 +
+// 12h ..), shifted by 16 bits for h = 0 so that the chunks are the five
+// consecutive 16-bit fields.
+template <bool FP4 = false>
 __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
   for (int q = tid; q < 2 * kWin; q += nthr) {
     const int h = q >= kWin ? 1 : 0, row = q - h * kWin;
@@ -291,9 +314,14 @@ __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, in
     }
     const uint32_t f[5] = {a, a >> 16, b, b >> 16, c};
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
-          make_uint4(bits4_to_bytes(f[i]), bits4_to_bytes(f[i] >> 4), bits4_to_bytes(f[i] >> 8), bits4_to_bytes(f[i] >> 12));
+    for (int i = 0; i < 5; ++i) {
+      if constexpr (FP4)
+        *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
+            make_uint2(bits8_to_nibbles(f[i]), bits8_to_nibbles(f[i] >> 8));
+      else
+        *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
+            make_uint4(bits4_to_bytes(f[i]), bits4_to_bytes(f[i] >> 4), bits4_to_bytes(f[i] >> 8), bits4_to_bytes(f[i] >> 12));
+    }
   }
 }
 
@@ -306,8 +334,10 @@ __device__ __forceinline__ uint32_t nib4_to_bytes(uint32_t a, uint32_t sel) {
 
 // Unpacks a four-bit window stage (160 rows of 96 bytes, window cell x' in
 // nibble x' % 2 of byte 8 + x' / 2) into the e4m3 window operand: 0x01 for
-// state 1, else 0.  Item = one 16-cell chunk of a row (eight source bytes);
-// consecutive threads take consecutive chunks of a row.
+// state 1, else 0 (FP4: the nibble flags are already the packed e2m1 unit).
+// Item = one 16-cell chunk of a row (eight source bytes); consecutive threads
+// take consecutive chunks of a row.
+template <bool FP4 = false>
 __device__ __forceinline__ void unpack_nib_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
   for (int q = tid; q < kWin * 10; q += nthr) {
     const int row = q / 10, c = q - row * 10;
@@ -320,9 +350,12 @@ __device__ __forceinline__ void unpack_nib_window(const uint8_t *xs, uint8_t *xe
       const uint32_t nz = (((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u;
       f[i] = (nz ^ 0x88888888u) >> 3;
     }
-    *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
-        make_uint4(nib4_to_bytes(f[0], 0x4140), nib4_to_bytes(f[0], 0x4342), nib4_to_bytes(f[1], 0x4140),
-                   nib4_to_bytes(f[1], 0x4342));
+    if constexpr (FP4)
+      *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint2(f[0], f[1]);
+    else
+      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
+          make_uint4(nib4_to_bytes(f[0], 0x4140), nib4_to_bytes(f[0], 0x4342), nib4_to_bytes(f[1], 0x4140),
+                     nib4_to_bytes(f[1], 0x4342));
   }
 }
 
@@ -337,9 +370,12 @@ __device__ __forceinline__ uint32_t bytes_to_nib_pairs(uint32_t w) { return w | 
 // 40 (e4m3).  Standard kernels hold the f16 band (FP16 kernel and pass 2 when
 // 2r+1 > 15) and, in the FP8 kernel, the e4m3 band, both with offset 16;
 // short-window kernels hold two e4m3 bands, offset 16 (pass 1) and offset 8
-// (pass 2).  Convert warp (q, kq) writes lanes 32q .. 32q+31 and every other
-// 8-column chunk from chunk kq.
-template <int DT, bool SW, bool WIDE = false>
+// (pass 2).  The FP4 kernel holds an e2m1 band (pass 1, in the f16 band's
+// columns; kind::f8f6f4 reads an e2m1 A operand from tensor memory as one
+// element per byte with the code in bits 2..5, so 1.0 = 0010b is 0x08) and
+// the e4m3 band (pass 2), both with offset 16.  Convert warp (q, kq) writes
+// lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
+template <int DT, bool SW, bool WIDE = false, bool FP4 = false>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
   using G = Geo<SW, WIDE>;
   using T = Tm<DT, SW, WIDE>;
@@ -347,18 +383,18 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
   // band (standard window; the FP16 kernel has only this one) and the e4m3
   // band, or in the short window the e4m3 bands of pass 1 and pass 2, or in
   // the wide tile the e4m3 band and the band of 16s (offset 32, rows 96..127
-  // zero)
-  constexpr int n0 = WIDE ? 5 : (SW ? 5 : 10), n = WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
+  // zero), or in the FP4 kernel the e2m1 and the e4m3 band
+  constexpr int n0 = (WIDE || FP4) ? 5 : (SW ? 5 : 10), n = (WIDE || FP4) ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
   for (int c = kq; c < n; c += 2) {                 // warp-uniform
     const bool first = c < n0;
-    const bool f16 = !SW && !WIDE && first;
+    const bool f16 = !SW && !WIDE && !FP4 && first;
     const int cc = first ? c : c - n0;
     const int off = WIDE ? G::kXOff : (SW && !first) ? G::kYOff : 16;
     const uint32_t col = WIDE ? (first ? T::kBand8 : T::kBand8x16)
                        : SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : T::kBand8);
-    const uint32_t one8 = (WIDE && !first) ? 0x58u : 0x38u;   // e4m3 16.0 or 1.0
+    const uint32_t one8 = (WIDE && !first) ? 0x58u : (FP4 && first) ? 0x08u : 0x38u;   // e4m3 16.0 or 1.0, e2m1 1.0
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -633,7 +669,8 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 // exceed 15 (e4m3 holds every integer multiple of 2^-9 up to 15 * 2^-9).
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
-template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS, bool WIDE = false, bool NIB = false>
+template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS, bool WIDE = false, bool NIB = false,
+          bool FP4 = false>
 __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   static_assert(!MS || !BATCH, "several steps per launch serve single instances");
   static_assert(!WIDE || (DT == 1 && !ENC && !BATCH && !SW && !BITS && !MS),
@@ -641,6 +678,8 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   static_assert(!BITS || (DT == 1 && ENC && !SW), "bit storage runs the FP8 kernel on a re-encoded window");
   static_assert(!NIB || (DT == 1 && ENC && !SW && !BITS && !WIDE && !BATCH && !MS),
                 "four-bit storage runs the FP8 kernel on a re-encoded window, single instance, one step per launch");
+  static_assert(!FP4 || (DT == 1 && ENC && !SW && !WIDE && !BATCH && !MS),
+                "FP4 operands: the FP8 kernel on a re-encoded window, single instance, one step per launch");
   static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
                 Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
   using L = Layout<DT, ENC, SW, BITS, WIDE, NIB>;
@@ -718,9 +757,9 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     const int s = j % L::NS, e = j % L::NE;
     if (!warp_wait(&bars->x_full[s], (j / L::NS) & 1, bars, p.timeout_ns)) return false;
     uint8_t *xe = smem + L::kXe + e * L::kXeStride;
-    if constexpr (BITS) unpack_window(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
-    else if constexpr (NIB) unpack_nib_window(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
-    else encode_window<L::E1>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, tid, nthr);
+    if constexpr (BITS) unpack_window<FP4>(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
+    else if constexpr (NIB) unpack_nib_window<FP4>(smem + L::kXs + s * L::kXsStride, xe, tid, nthr);
+    else encode_window<L::E1, FP4>(smem + L::kXs + s * L::kXsStride, xe, tile_rule<BATCH>(p, first, j).C > 2, tid, nthr);
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) { mbar_arrive(&bars->enc_full[e]); mbar_arrive(&bars->x_empty[s]); }
@@ -774,8 +813,9 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     if (lane == 0) {
       // f16 accumulators: every partial sum is a multiple of the operand scale
       // up to 1089 * scale, which f16 represents exactly
-      const uint32_t idesc1 = idesc_f16acc(128, G::kRows);
-      const uint32_t band1 = tmem + (DT == 1 ? T::kBand8 : T::kBand16);
+      // (FP4: e2m1 window and band, the band in the f16 band's columns)
+      const uint32_t idesc1 = idesc_f16acc(128, G::kRows) | (FP4 ? kIdescE2M1 : 0u);
+      const uint32_t band1 = tmem + ((DT == 1 && !FP4) ? T::kBand8 : T::kBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -908,7 +948,15 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         const OpDesc hop{hop0.d128 + hoff, hop0.d32 + hoff};
         const uint32_t d2 = tmem + T::kD2Base + reg * T::kD2Cols;
         const int rj = tile_rule<BATCH>(p, first, j).r;
-        if constexpr (DEC) {
+        if constexpr (FP4) {
+          // S = band x (H & 15) + band x (H - (H & 15)), both e4m3 halves of
+          // the H buffer, the second only when H can exceed 15
+          band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
+          if (2 * rj + 1 > 15) {
+            constexpr uint64_t kHi = (uint64_t)((kTile * kWin) >> 4);
+            band_mma<1, kTile, 1, true>(d2, band8, OpDesc{hop.d128 + kHi, hop.d32 + kHi}, idesc2);
+          }
+        } else if constexpr (DEC) {
           // S = band x (H & 15) + (16 band) x (H >> 4), the second only when H
           // can exceed 15; both e4m3 halves of the H buffer
           band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
@@ -949,7 +997,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
     // the bands for the first tile
-    store_bands<DT, SW, WIDE>(tmem, r0, q, kq, lane);
+    store_bands<DT, SW, WIDE, FP4>(tmem, r0, q, kq, lane);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -985,7 +1033,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           if (!ok) break;
         }
         tc_fence_after();
-        store_bands<DT, SW, WIDE>(tmem, rj, q, kq, lane);
+        store_bands<DT, SW, WIDE, FP4>(tmem, rj, q, kq, lane);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -1015,7 +1063,29 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           if (c == 4 && !last) break;
-          if constexpr (DEC) {
+          if constexpr (FP4) {
+            // D1 holds 0.5 H (e2m1 products), and 0.5 H * 2 + 1024 is exactly
+            // 1024 + H, an f16 whose low byte is H.  e4m3 digits: lo = H & 15,
+            // the code of itself times 2^-9, and hi = H - lo (0, 16 or 32:
+            // codes 0x10 and 0x18, the e4m3 numbers 16 * 2^-9 and 32 * 2^-9)
+            const __half2 k2 = __float2half2_rn(2.0f), k1024 = __float2half2_rn(1024.0f);
+            uint32_t e[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k2, k1024)),
+                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k2, k1024)), 0x6420);
+            *reinterpret_cast<uint4 *>(hop + off8[c]) =
+                make_uint4(e[0] & 0x0F0F0F0Fu, e[1] & 0x0F0F0F0Fu, e[2] & 0x0F0F0F0Fu, e[3] & 0x0F0F0F0Fu);
+            if (split) {
+              uint32_t hi[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const uint32_t t = e[i] & 0x30303030u;
+                hi[i] = t - ((t >> 2) & 0x08080808u);
+              }
+              *reinterpret_cast<uint4 *>(hop + kTile * kWin + off8[c]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            }
+          } else if constexpr (DEC) {
             // e4m3 digits H & 15 and H >> 4 (at most 4): each the code of
             // itself times 2^-9 (e4m3 subnormals for 1..7)
             const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
@@ -1260,6 +1330,18 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_tc_kernel(const __grid_consta
 // single it out.
 __global__ void __launch_bounds__(kThreads, 1) ltl_bits_kernel(const __grid_constant__ TcParams p) {
   ltl_tc_body<1, true, false, false, true, false>(p);
+}
+
+// FP4 (e2m1) pass-1 operands on the re-encoded window, pass 2 on e4m3 digits:
+// uint8, one-bit and four-bit storage.
+__global__ void __launch_bounds__(kThreads, 1) ltl_fp4_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, true, false, false, false, false, false, false, true>(p);
+}
+__global__ void __launch_bounds__(kThreads, 1) ltl_fp4_bits_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, true, false, false, true, false, false, false, true>(p);
+}
+__global__ void __launch_bounds__(kThreads, 1) ltl_fp4_nib_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, true, false, false, false, false, false, true, true>(p);
 }
 
 // Four bits per cell (C <= 16): the same body under its own name.
@@ -1639,6 +1721,24 @@ cudaError_t nib_launch(const TcParams &p, int grid, cudaStream_t s) {
     configured = true;
   }
   tc::ltl_nib_kernel<<<grid, tc::kThreads, L::kDyn, s>>>(p);
+  return cudaGetLastError();
+}
+
+// FP4 operands: the maps of the FP8 kernel for the same storage (0 = uint8,
+// 1 = one bit, 2 = four bits per cell).
+cudaError_t fp4_launch(const TcParams &p, int storage, int grid, cudaStream_t s) {
+  static bool configured[3] = {false, false, false};
+  void (*kern)(TcParams) = storage == 1 ? tc::ltl_fp4_bits_kernel : storage == 2 ? tc::ltl_fp4_nib_kernel : tc::ltl_fp4_kernel;
+  const size_t smem = storage == 1 ? tc::Layout<1, true, false, true>::kDyn
+                    : storage == 2 ? tc::Layout<1, true, false, false, false, true>::kDyn
+                                   : tc::Layout<1, true>::kDyn;
+  if (storage < 0 || storage > 2) return cudaErrorInvalidValue;
+  if (!configured[storage]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[storage] = true;
+  }
+  kern<<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

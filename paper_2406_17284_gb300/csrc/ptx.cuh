@@ -283,5 +283,8 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t M, uint32_t N) {
 __host__ __device__ constexpr uint32_t idesc_f16acc(uint32_t M, uint32_t N) {
   return ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+// kind::f8f6f4 with A and B format 5 (E2M1) instead of 0 (E4M3); OR into one
+// of the above.
+constexpr uint32_t kIdescE2M1 = (5u << 7) | (5u << 10);
 
 }  // namespace cat

@@ -44,7 +44,7 @@ CASES = [  # H, W, r, steps
 ]
 
 
-@pytest.mark.parametrize("dtype", ["fp8", "fp16"])
+@pytest.mark.parametrize("dtype", ["fp8", "fp16", "fp4"])
 def test_periodic_steps_match_oracle(cat, dtype):
     for H, W, r, steps in CASES:
         rule = inputs.scaled_rule(r, M=1)

@@ -1,8 +1,9 @@
 """Operand precisions on the 32768^2 workload: p = 0.35, the scaled rule (C2 M1),
 r in {1, 5, 10, 16}, 50 steps from the same seeded state with the tcgen05 FP8
-kernel (e4m3 operands) on uint8 and on one-bit storage, the tcgen05 FP16
+kernel (e4m3 operands) and the tcgen05 FP4 kernel (e2m1 pass-1 operands, e4m3
+digits in pass 2), each on uint8 and on one-bit storage, the tcgen05 FP16
 kernel and the INT8 fragment kernel (mma.sync m16n8k32; sm_103a has no tcgen05
-kind::i8).  All four must hold the same grid, bit for bit (the one-bit grid
+kind::i8).  All six must hold the same grid, bit for bit (the one-bit grids
 compared as packed rows), after 49 and after 50 steps, and step 50 is checked
 against the oracle on 64 random 256 x 256 windows (Sec. V-A: the method is
 exact, so every precision reaches the one correct result).
@@ -16,7 +17,7 @@ from paper_2406_17284_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 N, STEPS, WINDOWS, WIN = 32768, 50, 64, 256
-KERNELS = [("tcgen05", "fp8"), ("tcgen05", "fp16"), ("mma_sync", "int8")]
+KERNELS = [("tcgen05", "fp8"), ("tcgen05", "fp16"), ("mma_sync", "int8"), ("tcgen05", "fp4")]
 
 
 def pack_rows(t):
@@ -45,8 +46,8 @@ def test_precisions_agree_and_match_oracle_32768(cat, r):
     orl = oracle.Rule(**{k: rule[k] for k in ("r", "C", "M", "s1", "s2", "b1", "b2")})
     init = inputs.bernoulli(N, N, 0.35, 3200 + r)
     grids = [cat.Grid(N, N, rule, kernel=k, dtype=d) for k, d in KERNELS]
-    bits = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8", storage=cat.STORE_BIT1)
-    grids.append(bits)
+    bits = [cat.Grid(N, N, rule, kernel="tcgen05", dtype=d, storage=cat.STORE_BIT1) for d in ("fp8", "fp4")]
+    grids += bits
     try:
         for g in grids:
             g.set_state(init)
@@ -56,7 +57,8 @@ def test_precisions_agree_and_match_oracle_32768(cat, r):
         ref = grids[0].state_tensor()
         for g, (k, d) in zip(grids[1:], KERNELS[1:]):
             assert torch.equal(g.state_tensor(), ref), f"{k}/{d} differs from tcgen05/fp8 after {STEPS - 1} steps"
-        assert torch.equal(bits.state_tensor(), pack_rows(ref)), f"one-bit storage differs after {STEPS - 1} steps"
+        for b, d in zip(bits, ("fp8", "fp4")):
+            assert torch.equal(b.state_tensor(), pack_rows(ref)), f"one-bit storage ({d}) differs after {STEPS - 1} steps"
         rng = np.random.default_rng(r)
         pos = [tuple(int(v) for v in rng.integers(0, N - WIN, 2)) for _ in range(WINDOWS)]
         pos[:4] = [(0, 0), (0, N - WIN), (N - WIN, 0), (N - WIN, N - WIN)]   # the four corners
@@ -70,7 +72,8 @@ def test_precisions_agree_and_match_oracle_32768(cat, r):
         ref = grids[0].state_tensor()
         for g, (k, d) in zip(grids[1:], KERNELS[1:]):
             assert torch.equal(g.state_tensor(), ref), f"{k}/{d} differs from tcgen05/fp8 after {STEPS} steps"
-        assert torch.equal(bits.state_tensor(), pack_rows(ref)), f"one-bit storage differs after {STEPS} steps"
+        for b, d in zip(bits, ("fp8", "fp4")):
+            assert torch.equal(b.state_tensor(), pack_rows(ref)), f"one-bit storage ({d}) differs after {STEPS} steps"
         for (y0, x0), (ya, xa, win) in zip(pos, befores):
             want = oracle.step(win, orl)[y0 - ya:y0 - ya + WIN, x0 - xa:x0 - xa + WIN]
             got = ref[y0:y0 + WIN, x0:x0 + WIN].cpu().numpy()
