@@ -94,6 +94,7 @@ std::vector<Cand> candidates(const InstanceInfo &f) {
       out.push_back({CAT_KERNEL_TCGEN05, dt, 96, 0, spl});
     }
   }
+  out.push_back({CAT_KERNEL_TCGEN05, CAT_DTYPE_FP4_E2M1, 128, 160, 1});
   out.push_back({CAT_KERNEL_MMA_SYNC, CAT_DTYPE_FP16, 0, 0, 1});
   out.push_back({CAT_KERNEL_MMA_SYNC, CAT_DTYPE_INT8, 0, 0, 1});
   out.push_back({CAT_KERNEL_STENCIL, CAT_DTYPE_AUTO, 0, 0, 1});
