@@ -210,6 +210,7 @@ struct Layout {
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
   static constexpr uint32_t kDyn = kBars + 512 + 1024;        // + alignment slack
   static_assert(kDyn <= 232448, "shared memory budget");
+  static_assert(kH >= kXs + NS * kXsStride && kH >= kXe + kXeBytes, "window stages and encoded windows end before H");
   static_assert(kXe % 1024 == 0 && kXeStride % 1024 == 0 && kH % 1024 == 0 && kRing % 1024 == 0 && kHBytes % 1024 == 0,
                 "swizzled operands start on 1024-byte boundaries");
 };
