@@ -748,6 +748,11 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // barriers and tensor memory are set up: the next kernel in the stream may
+  // start its own set-up, and this one reads and writes global memory only
+  // once the previous kernel has completed
+  griddep_launch_dependents();
+  griddep_wait();
   const uint32_t tmem = bars->tmem_base;
   const uint32_t s_base = smem_u32(smem);
 
@@ -1467,6 +1472,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_vn_kernel(const __grid_consta
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  griddep_launch_dependents();   // as in the Moore body: set up, then wait for the previous kernel
+  griddep_wait();
   const uint32_t tmem = bars->tmem_base;
   const uint32_t s_base = smem_u32(smem);
 
@@ -1669,6 +1676,25 @@ size_t tc_smem_bytes(int dt, bool encode, bool sw) {
   return encode ? tc::Layout<1, true>::kDyn : tc::Layout<1, false>::kDyn;
 }
 
+// One-step kernels are launched with the programmatic-stream-serialization
+// attribute: the kernel may be scheduled while the previous kernel in the
+// stream drains (its CTAs start on SMs as the previous grid's CTAs leave
+// them), sets up its barriers and tensor memory, and waits for the previous
+// grid's completion (griddepcontrol.wait) before any global memory access.
+static cudaError_t launch_pdl(void (*kern)(TcParams), int grid, size_t smem, cudaStream_t s, const TcParams &p) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(tc::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 template <int DT, bool ENC, bool BATCH, bool SW = false, bool BITS = false>
 static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
   static bool configured = false;
@@ -1693,6 +1719,7 @@ static cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s) {
       void *args[] = {const_cast<TcParams *>(&p)};
       return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(multi), dim3(grid), dim3(tc::kThreads), args, smem, s);
     }
+    return launch_pdl(kern, grid, smem, s, p);
   }
   kern<<<grid, tc::kThreads, smem, s>>>(p);
   return cudaGetLastError();
@@ -1721,8 +1748,7 @@ cudaError_t nib_launch(const TcParams &p, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_nib_kernel<<<grid, tc::kThreads, L::kDyn, s>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(tc::ltl_nib_kernel, grid, L::kDyn, s, p);
 }
 
 // FP4 operands: the maps of the FP8 kernel for the same storage (0 = uint8,
@@ -1739,8 +1765,7 @@ cudaError_t fp4_launch(const TcParams &p, int storage, int grid, cudaStream_t s)
     if (e != cudaSuccess) return e;
     configured[storage] = true;
   }
-  kern<<<grid, tc::kThreads, smem, s>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, smem, s, p);
 }
 
 // The 96 x 96 tile: map_in_a / map_in_b are the 128 x 160 and 32 x 160 window
@@ -1754,8 +1779,7 @@ cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_wide_kernel<<<grid, tc::kThreads, L::kDyn, s>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(tc::ltl_wide_kernel, grid, L::kDyn, s, p);
 }
 
 // Simplified von Neumann neighbourhood: FP8, two-state rules, single instance
@@ -1768,8 +1792,7 @@ cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc::ltl_vn_kernel<<<grid, tc::kThreads, tc::vn::kDyn, s>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(tc::ltl_vn_kernel, grid, tc::vn::kDyn, s, p);
 }
 
 cudaError_t tc_launch_batch(const TcParams &p, int dt, bool encode, bool sw, int grid, cudaStream_t s) {
