@@ -262,24 +262,44 @@ __device__ __forceinline__ uint32_t bits8_to_nibbles(uint32_t b) {
 // Encodes the 160 x 160 u8 window xs as operand values: alive (state 1) ->
 // 0x01 (e4m3 2^-9, FP8 kernel), f16 1.0 (FP16 kernel) or e2m1 0.5 (FP4
 // kernel, packed units), anything else -> 0.
+// FP8 and FP4: the encoded window has the raw window's layout unit for unit
+// (a swizzle moves whole 16-byte units, and a unit holds 16 consecutive cells
+// of one row), so the buffer is encoded as a flat array of units: consecutive
+// threads take consecutive units (no bank conflicts, no address arithmetic
+// beyond the index).  The state-1 test per byte: x = w ^ 0x01 is zero exactly
+// where the state is 1, and bit 7 of ((x & 0x7F) + 0x7F) | x is set exactly
+// where x is not zero (no carry leaves a byte).
 template <int E, bool FP4 = false>
 __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bool multistate,
                                               int tid, int nthr) {
-  // consecutive threads take consecutive rows of one 16-byte column chunk, so
-  // every warp access touches each bank group evenly under both swizzles
-  for (int q = tid; q < kWin * 10; q += nthr) {
-    const int c = q / kWin, row = q - c * kWin;
-    uint4 v = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, row, 16 * c));
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    if (multistate) {
+  constexpr int kUnits = kWin * 10;
+  if constexpr (E == 1) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+    for (int q = tid; q < kUnits; q += nthr) {
+      const uint4 v = src[q];
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      if (multistate) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) w[i] = __vcmpeq4(w[i], 0x01010101u) & 0x01010101u;
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t x = w[i] ^ 0x01010101u;
+          w[i] = ((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) >> 7 & 0x01010101u) ^ 0x01010101u;
+        }
+      }
+      if constexpr (FP4) reinterpret_cast<uint2 *>(xe)[2 * q] = fp4_unit(w);
+      else reinterpret_cast<uint4 *>(xe)[q] = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    if constexpr (FP4) {
-      *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * c)) = fp4_unit(w);
-    } else if constexpr (E == 1) {
-      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
+  } else {
+    // f16 operands take two units per source unit: positions through op_off;
+    // consecutive threads take consecutive rows of one 16-byte column chunk,
+    // so every warp access touches each bank group evenly under both swizzles
+    for (int q = tid; q < kUnits; q += nthr) {
+      const int c = q / kWin, row = q - c * kWin;
+      uint4 v = *reinterpret_cast<const uint4 *>(xs + op_off(kWin, 1, row, 16 * c));
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      if (multistate) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = __vcmpeq4(w[i], 0x01010101u) & 0x01010101u;
+      }
       uint32_t h[8];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
