@@ -356,27 +356,34 @@ __device__ __forceinline__ uint32_t nib4_to_bytes(uint32_t a, uint32_t sel) {
 // Unpacks a four-bit window stage (160 rows of 96 bytes, window cell x' in
 // nibble x' % 2 of byte 8 + x' / 2) into the e4m3 window operand: 0x01 for
 // state 1, else 0 (FP4: the nibble flags are already the packed e2m1 unit).
-// Item = one 16-cell chunk of a row (eight source bytes); consecutive threads
-// take consecutive chunks of a row.
+// Item = two 16-cell units of a row (16 source bytes): units 2p and 2p + 1
+// sit in the two halves of one 32-byte slot under either swizzle (their
+// positions differ in the lowest bit), so the second offset is the first
+// XOR 16; consecutive threads take consecutive items of a row.
 template <bool FP4 = false>
 __device__ __forceinline__ void unpack_nib_window(const uint8_t *xs, uint8_t *xe, int tid, int nthr) {
-  for (int q = tid; q < kWin * 10; q += nthr) {
-    const int row = q / 10, c = q - row * 10;
-    const uint2 v = *reinterpret_cast<const uint2 *>(xs + row * 96 + 8 + 8 * c);
-    uint32_t f[2];
-    const uint32_t w[2] = {v.x, v.y};
+  for (int q = tid; q < kWin * 5; q += nthr) {
+    const int row = q / 5, pr = q - row * 5;
+    const uint2 *src = reinterpret_cast<const uint2 *>(xs + row * 96 + 8 + 16 * pr);
+    const uint2 a = src[0], b = src[1];
+    const uint32_t w[4] = {a.x, a.y, b.x, b.y};
+    uint32_t f[4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {   // nibble 1 where the state is 1 (borrow-free nibble test)
+    for (int i = 0; i < 4; ++i) {   // nibble 1 where the state is 1 (borrow-free nibble test)
       const uint32_t x = w[i] ^ 0x11111111u;
       const uint32_t nz = (((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u;
       f[i] = (nz ^ 0x88888888u) >> 3;
     }
-    if constexpr (FP4)
-      *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * c)) = make_uint2(f[0], f[1]);
-    else
-      *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * c)) =
-          make_uint4(nib4_to_bytes(f[0], 0x4140), nib4_to_bytes(f[0], 0x4342), nib4_to_bytes(f[1], 0x4140),
-                     nib4_to_bytes(f[1], 0x4342));
+    const uint32_t o0 = op_off(kWin, 1, row, 32 * pr), o1 = o0 ^ 16u;
+    if constexpr (FP4) {
+      *reinterpret_cast<uint2 *>(xe + o0) = make_uint2(f[0], f[1]);
+      *reinterpret_cast<uint2 *>(xe + o1) = make_uint2(f[2], f[3]);
+    } else {
+      *reinterpret_cast<uint4 *>(xe + o0) = make_uint4(nib4_to_bytes(f[0], 0x4140), nib4_to_bytes(f[0], 0x4342),
+                                                       nib4_to_bytes(f[1], 0x4140), nib4_to_bytes(f[1], 0x4342));
+      *reinterpret_cast<uint4 *>(xe + o1) = make_uint4(nib4_to_bytes(f[2], 0x4140), nib4_to_bytes(f[2], 0x4342),
+                                                       nib4_to_bytes(f[3], 0x4140), nib4_to_bytes(f[3], 0x4342));
+    }
   }
 }
 
@@ -537,6 +544,25 @@ __device__ __forceinline__ uint32_t rule4_multistate_h(uint32_t s01, uint32_t s2
   const uint32_t inc = cw + 0x01010101u;                            // c + 1 <= C <= 255: no carries
   const uint32_t aged = inc & (nonzero_bytes(inc ^ Cb) * 0xFFu);    // c + 1, or 0 where c + 1 == C
   return (inr & dead) | ((0x02020202u - inr) & (alive * 0xFFu)) | (aged & (dying * 0xFFu));
+}
+
+// As rule4_multistate_h for C <= 128, with fewer operations: every state is
+// below 128, so adding up to 0x7F to a byte carries into no other byte and
+// bit 7 of the sum is a comparison: c >= 1 (c + 0x7F), c >= 2 (c + 0x7E),
+// c + 1 >= C (c + 1 + Kc, Kc = 0x80 - C in every byte).  A cell alive (c = 1)
+// becomes inr ? 1 : 2 = inr + 2 (1 - inr); a dead one inr; a dying one c + 1,
+// or 0 at C.
+__device__ __forceinline__ uint32_t rule4_multistate_small_h(uint32_t s01, uint32_t s23, uint32_t cw,
+                                                             const HalfRule &h, uint32_t Kc) {
+  const uint32_t ge1 = ((cw + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+  const uint32_t ge2 = ((cw + 0x7E7E7E7Eu) >> 7) & 0x01010101u;
+  const uint32_t inr = rule4_binary_h(s01, s23, ge1, h);
+  const uint32_t r01 = inr + 2u * (ge1 & ~ge2 & ~inr);
+  const uint32_t inc = cw + 0x01010101u;
+  const uint32_t wrap = ((inc + Kc) >> 7) & 0x01010101u;
+  const uint32_t aged = inc & ~(wrap * 0xFFu);
+  const uint32_t dm = ge2 * 0xFFu;
+  return (aged & dm) | (r01 & ~dm);
 }
 
 // The rule's two ranges scaled like a wide tile's f32 accumulator (S * scale,
@@ -1271,7 +1297,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           // 16 cells of a chunk are 8 bytes of the row, cell 2i in the low
           // nibble of byte i; the ring row is 64 bytes, 64B-swizzled (16-byte
           // unit u of row y at u ^ ((y >> 1) & 3)); cells at x >= W stay 0
-          const uint32_t Cb = (uint32_t)R.C * 0x01010101u;
+          const uint32_t Kc = (uint32_t)((0x80 - R.C) & 0xFF) * 0x01010101u;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int cc = kq + 4 * c;
@@ -1281,9 +1307,9 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
                                     nib4_to_bytes(cv.y, 0x4140), nib4_to_bytes(cv.y, 0x4342)};
             uint32_t ns[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)   // C <= 16 here
               ns[i] = bytes_to_nib_pairs(R.C == 2 ? rule4_binary_h(v[c][2 * i], v[c][2 * i + 1], st[i], hr)
-                                                  : rule4_multistate_h(v[c][2 * i], v[c][2 * i + 1], st[i], hr, Cb));
+                                                  : rule4_multistate_small_h(v[c][2 * i], v[c][2 * i + 1], st[i], hr, Kc));
             uint2 ov = make_uint2(__byte_perm(ns[0], ns[1], 0x6420), __byte_perm(ns[2], ns[3], 0x6420));
             const int lim = t.W - (t.x0 + 16 * cc);
             if (lim < 16) {
@@ -1306,15 +1332,23 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           }
         } else if (!sums_mode) {
           const uint32_t Cb = (uint32_t)R.C * 0x01010101u;
+          const uint32_t Kc = (uint32_t)((0x80 - R.C) & 0xFF) * 0x01010101u;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             uint4 *cell = reinterpret_cast<uint4 *>(ring + off_c[c]);
             const uint4 cv = *cell;
             uint4 ov;
-            ov.x = rule4_multistate_h(v[c][0], v[c][1], cv.x, hr, Cb);
-            ov.y = rule4_multistate_h(v[c][2], v[c][3], cv.y, hr, Cb);
-            ov.z = rule4_multistate_h(v[c][4], v[c][5], cv.z, hr, Cb);
-            ov.w = rule4_multistate_h(v[c][6], v[c][7], cv.w, hr, Cb);
+            if (R.C <= 128) {
+              ov.x = rule4_multistate_small_h(v[c][0], v[c][1], cv.x, hr, Kc);
+              ov.y = rule4_multistate_small_h(v[c][2], v[c][3], cv.y, hr, Kc);
+              ov.z = rule4_multistate_small_h(v[c][4], v[c][5], cv.z, hr, Kc);
+              ov.w = rule4_multistate_small_h(v[c][6], v[c][7], cv.w, hr, Kc);
+            } else {
+              ov.x = rule4_multistate_h(v[c][0], v[c][1], cv.x, hr, Cb);
+              ov.y = rule4_multistate_h(v[c][2], v[c][3], cv.y, hr, Cb);
+              ov.z = rule4_multistate_h(v[c][4], v[c][5], cv.z, hr, Cb);
+              ov.w = rule4_multistate_h(v[c][6], v[c][7], cv.w, hr, Cb);
+            }
             *cell = ov;
           }
         } else {   // box counts

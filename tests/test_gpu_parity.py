@@ -148,9 +148,14 @@ def test_paper_table_iv_rules(cat, kernel, dtype):
 
 @pytest.mark.parametrize("kernel,dtype", KERNELS, ids=KIDS)
 def test_multistate_decay(cat, kernel, dtype):
-    """Only state 1 is counted; states 2..C-1 decay (R10 C16 and small C)."""
+    """Only state 1 is counted; states 2..C-1 decay (R10 C16, small C, and C =
+    128, 200, 255 around the tcgen05 epilogue's two formulations, C <= 128 and
+    C > 128)."""
     cases = [(inputs.MULTISTATE_R10_C16, 16), (dict(r=3, C=3, M=0, s1=10, s2=25, b1=9, b2=14), 3),
-             (dict(r=16, C=5, M=1, s1=300, s2=700, b1=320, b2=500), 5)]
+             (dict(r=16, C=5, M=1, s1=300, s2=700, b1=320, b2=500), 5),
+             (dict(r=5, C=128, M=1, s1=3, s2=40, b1=2, b2=30), 128),
+             (dict(r=9, C=200, M=0, s1=2, s2=90, b1=1, b2=60), 200),
+             (dict(r=2, C=255, M=1, s1=1, s2=9, b1=1, b2=6), 255)]
     for rule, C in cases:
         grid = inputs.uniform_states(290, 310, C, 17 + C)
         want = oracle.step(grid, orule(rule), n_steps=5)
