@@ -170,6 +170,14 @@ def measured_peaks():
 FLOPS_PER_CELL = 192.0
 
 
+def executed_flops_per_cell(short_window: bool) -> float:
+    """Tensor flops the tcgen05 Moore kernel issues per cell update, from its
+    instruction shapes: pass 1 M = 128, N = 160 (144 in the short window),
+    K = 160 and pass 2 M = N = 128, K = 160 per 128 x 128 tile."""
+    n1 = 144 if short_window else 160
+    return (2 * 128 * n1 * 160 + 2 * 128 * 128 * 160) / (128 * 128)
+
+
 def measure_tensor_peaks(torch, cat, stream):
     """Dense tcgen05 MMA rates of this GPU (cat_tensor_probe: one CTA per SM issuing
     M=128 N=256 MMAs back to back): burst = median of ten ~2 ms launches,
@@ -818,6 +826,10 @@ def run_cat(args, rank, world, local):
                          "kernel_time_share": share[dom] / sum(share.values()),
                          "hbm_term_cell_updates_per_s": dom_roof["hbm_term"],
                          "tensor_term_cell_updates_per_s": dom_roof["tensor_term"],
+                         "executed_flops_per_cell": executed_flops_per_cell("short" in dom),
+                         "executed_tflops": n * n / (dom_ms / 1000.0) * executed_flops_per_cell("short" in dom) / 1e12,
+                         "executed_frac_of_tensor_peak": n * n / (dom_ms / 1000.0) * executed_flops_per_cell("short" in dom)
+                                                         / (tpeak * 1e12),
                          "tensor_term": f"{FLOPS_PER_CELL:.0f} flops per cell update at the measured "
                                         f"{'e4m3' if args.dtype == 'fp8' else 'f16'} burst rate {tpeak:.0f} TFLOP/s",
                          "all_radii": {"achieved": achieved_all, "frac": achieved_all / hbm}},
