@@ -810,7 +810,8 @@ def run_cat(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": ("e4m3" if args.dtype == "fp8" else "f16") + " operands, f16 accumulators (exact), u8 states",
+            "dtype": "e4m3" if args.dtype == "fp8" else "f16",
+            "dtype_detail": ("e4m3" if args.dtype == "fp8" else "f16") + " operands, f16 accumulators (exact), u8 states",
             "data": "synthetic",
             "config": {"workload": f"radius_sweep_{n}x{n}_r1-16_bernoulli0.5", "grid": [n, n], "radii": RADII,
                        "rule": "R_r C2 M1 S0.34n..0.58n B0.34n..0.45n NM", "boundary": "zero",
