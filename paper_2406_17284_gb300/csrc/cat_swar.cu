@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(kBlock) ltl_swar_kernel(const SwarParams p) {
   const uint32_t nmask = nc == p.words - 1 ? last_mask : ~0u;
   const uint32_t *in_c = p.in + (col ? wi : 0), *in_n = p.in + (nc_ok ? nc : 0);
   const RangeBits<NS> surv = range_bits<NS>(p.rule.s_lo, p.rule.s_w), born = range_bits<NS>(p.rule.b_lo, p.rule.b_w);
+  // programmatic dependent launch: the next kernel may be scheduled, and the
+  // grid is read only once the previous kernel (the step that wrote it) is done
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // horizontal sums of row y for this thread's 32 cells (every lane takes part)
   auto hsum = [&](int y, uint32_t (&h)[NH], uint32_t &centre) {
@@ -218,6 +222,8 @@ __global__ void __launch_bounds__(kTbThreads) ltl_swar_tb_kernel(const SwarParam
   const bool col = wi >= 0 && wi < p.words;
   const uint32_t mask = !col ? 0u : (wi == p.words - 1 && last_bits < 32) ? (1u << last_bits) - 1u : ~0u;
   const RangeBits<NS> surv = range_bits<NS>(p.rule.s_lo, p.rule.s_w), born = range_bits<NS>(p.rule.b_lo, p.rule.b_w);
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // as in ltl_swar_kernel
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int i = 0; i < rows; ++i) {
     const int64_t y = y0 - halo + i;
     buf[0][i][c] = (col && y >= 0 && y < p.H) ? __ldg(p.in + y * p.pitch_words + wi) & mask : 0u;
@@ -277,6 +283,22 @@ __global__ void __launch_bounds__(kTbThreads) ltl_swar_tb_kernel(const SwarParam
   }
 }
 
+// Launch configuration with programmatic stream serialization: the kernels
+// above wait for the previous kernel in the stream before reading the grid.
+cudaLaunchConfig_t pdl_config(dim3 grid, int threads, size_t smem, cudaStream_t s) {
+  static cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 }  // namespace
 
 cudaError_t swar_tb_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
@@ -310,8 +332,8 @@ cudaError_t swar_tb_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64
     if (e != cudaSuccess) return e;
     configured[rule.r] = true;
   }
-  kern<<<grid, kTbThreads, kTbSmem, s>>>(p, k);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = pdl_config(grid, kTbThreads, kTbSmem, s);
+  return cudaLaunchKernelEx(&cfg, kern, p, k);
 }
 
 cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t H, int64_t W, const RuleDev &rule,
@@ -328,15 +350,17 @@ cudaError_t swar_launch(const uint8_t *in, uint8_t *out, int64_t pitch, int64_t 
   p.sums_ld = sums_ld;
   const int64_t strips = (H + kRows - 1) / kRows;
   const dim3 grid((unsigned)((p.words + kBlock - 1) / kBlock), (unsigned)(strips < 65535 ? strips : 65535));
+  void (*kern)(SwarParams) = nullptr;
   switch (rule.r) {
-    case 1: ltl_swar_kernel<1><<<grid, kBlock, 0, s>>>(p); break;
-    case 2: ltl_swar_kernel<2><<<grid, kBlock, 0, s>>>(p); break;
-    case 3: ltl_swar_kernel<3><<<grid, kBlock, 0, s>>>(p); break;
-    case 4: ltl_swar_kernel<4><<<grid, kBlock, 0, s>>>(p); break;
-    case 5: ltl_swar_kernel<5><<<grid, kBlock, 0, s>>>(p); break;
+    case 1: kern = ltl_swar_kernel<1>; break;
+    case 2: kern = ltl_swar_kernel<2>; break;
+    case 3: kern = ltl_swar_kernel<3>; break;
+    case 4: kern = ltl_swar_kernel<4>; break;
+    case 5: kern = ltl_swar_kernel<5>; break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = pdl_config(grid, kBlock, 0, s);
+  return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 }  // namespace cat
