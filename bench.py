@@ -689,31 +689,36 @@ def run_cat(args, rank, world, local):
     # pinned buffers).
     pin_in = torch.from_numpy(host).pin_memory()
     pin_out = [torch.empty_like(pin_in).pin_memory() for _ in range(2)]
-    e2e_steps = max(1, min(args.steps, 3))
+    # (the host link's rate varies between runs: the best of three runs of up
+    # to three steps each is reported)
+    e2e_steps, e2e_runs = max(1, min(args.steps, 3)), 3
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    read_out = {r: None for r in RADII}
-    torch.cuda.synchronize()
-    te0 = time.perf_counter()
-    k = 0
-    for _ in range(e2e_steps):
-        for r in RADII:
-            g = grids[r]
-            if read_out[r] is not None:
-                s_in.wait_event(read_out[r])
-            cat.cat_set_state(g.handle, pin_in.data_ptr(), n, False, s_in)
-            copied = torch.cuda.Event()
-            copied.record(s_in)
-            stream.wait_event(copied)
-            g.step(1, stream)
-            stepped = torch.cuda.Event()
-            stepped.record(stream)
-            s_out.wait_event(stepped)
-            cat.cat_get_state(g.handle, pin_out[k & 1].data_ptr(), n, False, s_out)
-            k += 1
-            read_out[r] = torch.cuda.Event()
-            read_out[r].record(s_out)
-    torch.cuda.synchronize()
-    te = (time.perf_counter() - te0) / e2e_steps
+    te_runs = []
+    for _ in range(e2e_runs):
+        read_out = {r: None for r in RADII}
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        k = 0
+        for _ in range(e2e_steps):
+            for r in RADII:
+                g = grids[r]
+                if read_out[r] is not None:
+                    s_in.wait_event(read_out[r])
+                cat.cat_set_state(g.handle, pin_in.data_ptr(), n, False, s_in)
+                copied = torch.cuda.Event()
+                copied.record(s_in)
+                stream.wait_event(copied)
+                g.step(1, stream)
+                stepped = torch.cuda.Event()
+                stepped.record(stream)
+                s_out.wait_event(stepped)
+                cat.cat_get_state(g.handle, pin_out[k & 1].data_ptr(), n, False, s_out)
+                k += 1
+                read_out[r] = torch.cuda.Event()
+                read_out[r].record(s_out)
+        torch.cuda.synchronize()
+        te_runs.append((time.perf_counter() - te0) / e2e_steps)
+    te = min(te_runs)
     e2e_value = cells_per_step * world / te
 
     link = host_link(torch, dev)
@@ -854,6 +859,8 @@ def run_cat(args, rank, world, local):
             "wide_radius": wide,
             "precisions": fp4,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": n * n * len(RADII),
+                    "runs_cell_updates_per_s": [cells_per_step * world / t for t in te_runs],
+                    "method": f"best of {e2e_runs} runs of {e2e_steps} steps",
                     "d2h_bytes_per_step": n * n * len(RADII), "host_link": link,
                     "link_bound_cell_updates_per_s": link["bidirectional_gbs_each_way"] * 1e9 * world},
             "cpu_baseline": cpu,
