@@ -565,39 +565,44 @@ __device__ __forceinline__ uint32_t rule4_multistate_small_h(uint32_t s01, uint3
   return (aged & dm) | (r01 & ~dm);
 }
 
-// The rule's two ranges scaled like a wide tile's f32 accumulator (S * scale,
-// counts up to 4225).  An empty range gets lo above hi, both above any count.
-struct FloatRule {
-  float bl, bh, sl, sh;
+// The rule's two ranges for the wide tile's integer test: the bounds of each
+// range as two 16-bit halves, the upper ones with bit 15 set.  An empty range
+// (or one starting above 4225, the largest count) gets lo = 0x7FFF.
+struct IntRule {
+  uint32_t bl2, bh2, sl2, sh2;
 };
 
-__device__ __forceinline__ FloatRule make_float_rule(const RuleDev &R, float scale) {
-  auto lo_of = [](int lo) { return lo > 4225 ? 65536.0f : (float)lo; };
-  auto hi_of = [](int lo, int w) { return lo > 4225 ? 32768.0f : fminf((float)lo + (float)w, 65536.0f); };
-  return FloatRule{lo_of(R.b_lo) * scale, hi_of(R.b_lo, R.b_w) * scale, lo_of(R.s_lo) * scale,
-                   hi_of(R.s_lo, R.s_w) * scale};
+__host__ __device__ __forceinline__ IntRule make_int_rule(const RuleDev &R) {
+  auto pair = [](int v) { return (uint32_t)v * 0x00010001u; };
+  auto lo_of = [](int lo) { return lo > 4225 ? 0x7FFF : (lo < 0 ? 0 : lo); };
+  auto hi_of = [](int lo, int w) {
+    const int64_t hi = (int64_t)lo + w;
+    return lo > 4225 ? 0 : (hi > 0x7FFF ? 0x7FFF : (hi < 0 ? 0 : (int)hi));
+  };
+  return IntRule{pair(lo_of(R.b_lo)), pair(hi_of(R.b_lo, R.b_w) | 0x8000), pair(lo_of(R.s_lo)),
+                 pair(hi_of(R.s_lo, R.s_w) | 0x8000)};
 }
 
-// 0xFF in byte k where float k is negative (its sign byte replicated by prmt).
-__device__ __forceinline__ uint32_t sign_bytes4(float a, float b, float c, float d) {
-  uint32_t lo, hi;
-  asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(lo) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
-  asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(hi) : "r"(__float_as_uint(c)), "r"(__float_as_uint(d)));
-  return __byte_perm(lo, hi, 0x5410);
-}
-
-// Next states of four cells of a two-state rule from their counts as f32
-// (S * scale) and their current states (bytes 0/1 of cw): both range tests
-// (s - lo)(hi - s) >= 0 per cell, as in rule4_binary_h (every nonzero factor
-// is a multiple of the scale, so no product underflows to zero), and the
-// centre picks survival or birth.
-__device__ __forceinline__ uint32_t rule4_binary_f(const float *s, uint32_t cw, const FloatRule &f) {
-  const uint32_t out_s = sign_bytes4((s[0] - f.sl) * (f.sh - s[0]), (s[1] - f.sl) * (f.sh - s[1]),
-                                     (s[2] - f.sl) * (f.sh - s[2]), (s[3] - f.sl) * (f.sh - s[3]));
-  const uint32_t out_b = sign_bytes4((s[0] - f.bl) * (f.bh - s[0]), (s[1] - f.bl) * (f.bh - s[1]),
-                                     (s[2] - f.bl) * (f.bh - s[2]), (s[3] - f.bl) * (f.bh - s[3]));
-  const uint32_t alive = cw * 0xFFu;
-  return ~((out_s & alive) | (out_b & ~alive)) & 0x01010101u;
+// Next states of four cells (bytes of cw, 0/1) of a two-state rule from their
+// counts as the wide tile's f32 accumulators (S * 2^-9, S <= 4225).  Adding
+// 16384 puts S in the low bits of the f32's mantissa (16384 + S * 2^-9 is
+// exact: the ulp at 2^14 is 2^-9), so one byte permute packs the counts of two
+// cells as 16-bit halves; per half, 0x8000 + S - lo and 0x8000 + hi - S stay
+// positive (no borrow crosses the halves) and their bit 15 says S >= lo and
+// S <= hi.  The range of each cell (survival if alive, birth if dead) is
+// picked per half by a byte permute with the state as selector, as in
+// rule4_binary_h.
+__device__ __forceinline__ uint32_t rule4_binary_i(const uint32_t *f4, uint32_t cw, const IntRule &ir) {
+  uint32_t s[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s[i] = __float_as_uint(__uint_as_float(f4[i]) + 16384.0f);
+  const uint32_t S01 = __byte_perm(s[0], s[1], 0x5410), S23 = __byte_perm(s[2], s[3], 0x5410);
+  const uint32_t selA = cw * 0x44u + 0x32103210u, selB = selA >> 16;
+  const uint32_t lo01 = __byte_perm(ir.bl2, ir.sl2, selA), hi01 = __byte_perm(ir.bh2, ir.sh2, selA);
+  const uint32_t lo23 = __byte_perm(ir.bl2, ir.sl2, selB), hi23 = __byte_perm(ir.bh2, ir.sh2, selB);
+  const uint32_t in01 = ((S01 | 0x80008000u) - lo01) & (hi01 - S01) & 0x80008000u;
+  const uint32_t in23 = ((S23 | 0x80008000u) - lo23) & (hi23 - S23) & 0x80008000u;
+  return (__byte_perm(in01, in23, 0x7531) >> 7) & 0x01010101u;   // bytes 1 and 3 of each: cells 0..3
 }
 
 __device__ __forceinline__ float half_lo(uint32_t h2) { return __low2float(as_h2(h2)); }
@@ -1191,7 +1196,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     const bool rows = q < 3;
     const int nch = kq + 4 < 6 ? 2 : 1;
     bool ok = true;
-    const FloatRule fr = make_float_rule(p.rule, kScale);
+    const IntRule ir = make_int_rule(p.rule);
     TileSeq<false, false, G::kTS> seq(p, first, n_my);
     for (int j = 0; ok && j < n_all; ++j, seq.next(p)) {
       const int reg = j % ND2, k = j % NR;
@@ -1216,14 +1221,11 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           if (!p.sums) {
             uint4 *cell = reinterpret_cast<uint4 *>(ring + y * G::kTS + 16 * cc);
             const uint4 cv = *cell;
-            float f[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[c][i]);
             uint4 ov;
-            ov.x = rule4_binary_f(f, cv.x, fr);
-            ov.y = rule4_binary_f(f + 4, cv.y, fr);
-            ov.z = rule4_binary_f(f + 8, cv.z, fr);
-            ov.w = rule4_binary_f(f + 12, cv.w, fr);
+            ov.x = rule4_binary_i(v[c], cv.x, ir);
+            ov.y = rule4_binary_i(v[c] + 4, cv.y, ir);
+            ov.z = rule4_binary_i(v[c] + 8, cv.z, ir);
+            ov.w = rule4_binary_i(v[c] + 12, cv.w, ir);
             *cell = ov;
           } else {   // box counts
             const int gy = t.y0 + y;
