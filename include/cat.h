@@ -192,7 +192,8 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
 
 /* Chooses the kernel, operand dtype and storage used by later steps
  * (defaults: CAT_KERNEL_AUTO -> TCGEN05, CAT_DTYPE_AUTO -> FP8_E4M3 for
- * TCGEN05, FP16 for MMA_SYNC; instances start with CAT_STORE_U8).  A change
+ * TCGEN05 (FP4_E2M1 for two-state rules on NIB4 storage), FP16 for
+ * MMA_SYNC; instances start with CAT_STORE_U8).  A change
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).
  * CAT_STORE_BIT1 needs C = 2, the zero boundary and TCGEN05 with FP8_E4M3 or
