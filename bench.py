@@ -381,8 +381,10 @@ def measure_multistate(args, torch, cat, inputs, stream):
     t = time_launches(torch, lambda: g.step(1, stream), 4, stream)
     out["single_cell_updates_per_s"] = n * n / (statistics.median(t) / 1000.0)
     g.close()
-    # the same grid stored four bits per cell (1 byte of state traffic per update)
-    g = cat.Grid(n, n, rule, kernel="tcgen05", dtype="fp8", storage=cat.STORE_NIB4)
+    # the same grid stored four bits per cell (1 byte of state traffic per update),
+    # on the operands CAT_DTYPE_AUTO takes there
+    g = cat.Grid(n, n, rule, kernel="tcgen05", dtype="auto", storage=cat.STORE_NIB4)
+    out["single_nib4_dtype"] = {v: k for k, v in cat.DTYPES.items()}[cat.cat_get_options(g.handle)["dtype"]]
     g.set_state(init)
     g.step(1, stream)
     t = time_launches(torch, lambda: g.step(1, stream), 4, stream)

@@ -98,8 +98,9 @@ enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
  *             16 elements packed into the first 8 bytes of each 16-byte unit)
  *             against an e2m1 band of ones, so pass 1 gives H / 2 exactly.
  *             H <= 33 is not an e2m1 number (the largest is 6), so pass 2
- *             takes H as two e4m3 digits, H & 15 and H - (H & 15), against
- *             the e4m3 band of ones: the e2m1 / e4m3 mix of kind::f8f6f4. */
+ *             runs as in FP8_E4M3: H as e4m3 for 2r+1 <= 15 (the e2m1 /
+ *             e4m3 mix of kind::f8f6f4), else H / 2 in f16 against an f16
+ *             band of 2^-8. */
 enum {
   CAT_DTYPE_AUTO = 0,
   CAT_DTYPE_FP16 = 1,
@@ -192,7 +193,7 @@ CAT_API int cat_create_ex(int64_t H, int64_t W, const cat_rule_t *rule, int32_t 
 
 /* Chooses the kernel, operand dtype and storage used by later steps
  * (defaults: CAT_KERNEL_AUTO -> TCGEN05, CAT_DTYPE_AUTO -> FP8_E4M3 for
- * TCGEN05 (FP4_E2M1 for two-state rules on NIB4 storage), FP16 for
+ * TCGEN05 (FP4_E2M1 on NIB4 storage), FP16 for
  * MMA_SYNC; instances start with CAT_STORE_U8).  A change
  * of storage reallocates both buffers and converts the current grid (the
  * device is synchronised; earlier cat_state_ptr addresses become invalid).

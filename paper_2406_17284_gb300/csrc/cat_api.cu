@@ -635,13 +635,13 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
            : storage == CAT_STORE_BIT1 && h->rule.r <= 5 && h->rule.C == 2 ? CAT_KERNEL_BITSLICE
                                                                           : CAT_KERNEL_TCGEN05;
   const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
-  // AUTO: FP8 on tcgen05 (FP4 for two-state rules on four-bit storage, whose
-  // nibble flags are the e2m1 operand as they stand: measured faster at every
-  // radius), FP16 on the fragment kernel
+  // AUTO: FP8 on tcgen05 (FP4 on four-bit storage, whose state-1 nibble
+  // flags are the e2m1 operand as they stand: measured faster at every radius
+  // and state count), FP16 on the fragment kernel
   if (dtype == CAT_DTYPE_AUTO)
     dtype = kernel != CAT_KERNEL_TCGEN05 ? CAT_DTYPE_FP16
-          : (storage == CAT_STORE_NIB4 && h->rule.C == 2 && !vn && !wide) ? CAT_DTYPE_FP4_E2M1
-                                                                            : CAT_DTYPE_FP8_E4M3;
+          : (storage == CAT_STORE_NIB4 && !vn && !wide) ? CAT_DTYPE_FP4_E2M1
+                                                          : CAT_DTYPE_FP8_E4M3;
   if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC");
   if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_FP4_E2M1 &&

@@ -398,31 +398,37 @@ __device__ __forceinline__ uint32_t bytes_to_nib_pairs(uint32_t w) { return w | 
 // 40 (e4m3).  Standard kernels hold the f16 band (FP16 kernel and pass 2 when
 // 2r+1 > 15) and, in the FP8 kernel, the e4m3 band, both with offset 16;
 // short-window kernels hold two e4m3 bands, offset 16 (pass 1) and offset 8
-// (pass 2).  The FP4 kernel holds an e2m1 band (pass 1, in the f16 band's
-// columns; kind::f8f6f4 reads an e2m1 A operand from tensor memory as one
-// element per byte with the code in bits 2..5, so 1.0 = 0010b is 0x08) and
-// the e4m3 band (pass 2), both with offset 16.  Convert warp (q, kq) writes
-// lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
+// (pass 2).  The FP4 kernel holds the FP8 kernel's two pass-2 bands, the f16
+// one with 2^-8 for one (its pass 1 leaves H / 2, not H * 2^-9), and an e2m1
+// band for pass 1 in the 40 columns after the e4m3 one (kind::f8f6f4 reads an
+// e2m1 A operand from tensor memory as one element per byte with the code in
+// bits 2..5, so 1.0 = 0010b is 0x08), all with offset 16.  Convert warp
+// (q, kq) writes lanes 32q .. 32q+31 and every other 8-column chunk from
+// chunk kq.
 template <int DT, bool SW, bool WIDE = false, bool FP4 = false>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
   using G = Geo<SW, WIDE>;
   using T = Tm<DT, SW, WIDE>;
-  // chunks [0, n0) belong to the first band, [n0, n) to the second: the f16
-  // band (standard window; the FP16 kernel has only this one) and the e4m3
-  // band, or in the short window the e4m3 bands of pass 1 and pass 2, or in
-  // the wide tile the e4m3 band and the band of 16s (offset 32, rows 96..127
-  // zero), or in the FP4 kernel the e2m1 and the e4m3 band
-  constexpr int n0 = (WIDE || FP4) ? 5 : (SW ? 5 : 10), n = (WIDE || FP4) ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
+  // chunks [0, n0) belong to the first band, [n0, n1) to the second, [n1, n)
+  // to a third: the f16 band (standard window; the FP16 kernel has only this
+  // one) and the e4m3 band, or in the short window the e4m3 bands of pass 1
+  // and pass 2, or in the wide tile the e4m3 band and the band of 16s (offset
+  // 32, rows 96..127 zero), or in the FP4 kernel the f16 band of 2^-8 (pass 2
+  // on H / 2), the e4m3 band and the e2m1 band (pass 1, after the e4m3 one)
+  constexpr int n0 = WIDE ? 5 : (SW ? 5 : 10), n1 = WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
+  constexpr int n = FP4 ? 20 : n1;
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
   for (int c = kq; c < n; c += 2) {                 // warp-uniform
-    const bool first = c < n0;
-    const bool f16 = !SW && !WIDE && !FP4 && first;
-    const int cc = first ? c : c - n0;
+    const bool first = c < n0, third = c >= n1;
+    const bool f16 = !SW && !WIDE && first;
+    const int cc = first ? c : third ? c - n1 : c - n0;
     const int off = WIDE ? G::kXOff : (SW && !first) ? G::kYOff : 16;
-    const uint32_t col = WIDE ? (first ? T::kBand8 : T::kBand8x16)
+    const uint32_t col = third ? T::kBand8 + 40
+                       : WIDE ? (first ? T::kBand8 : T::kBand8x16)
                        : SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : T::kBand8);
-    const uint32_t one8 = (WIDE && !first) ? 0x58u : (FP4 && first) ? 0x08u : 0x38u;   // e4m3 16.0 or 1.0, e2m1 1.0
+    const uint32_t one8 = third ? 0x08u : (WIDE && !first) ? 0x58u : 0x38u;   // e2m1 1.0, e4m3 16.0 or 1.0
+    const uint32_t one16 = FP4 ? 0x1C00u : 0x3C00u;                             // f16 2^-8 or 1.0
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -432,7 +438,7 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const int d = k0 + b - m;
-          if (d >= off - r && d <= off + r) w |= 0x3C00u << (16 * b);
+          if (d >= off - r && d <= off + r) w |= one16 << (16 * b);
         }
       } else if (m < G::kTS) {
 #pragma unroll
@@ -870,9 +876,9 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     if (lane == 0) {
       // f16 accumulators: every partial sum is a multiple of the operand scale
       // up to 1089 * scale, which f16 represents exactly
-      // (FP4: e2m1 window and band, the band in the f16 band's columns)
+      // (FP4: e2m1 window and band, the band after the e4m3 one)
       const uint32_t idesc1 = idesc_f16acc(128, G::kRows) | (FP4 ? kIdescE2M1 : 0u);
-      const uint32_t band1 = tmem + ((DT == 1 && !FP4) ? T::kBand8 : T::kBand16);
+      const uint32_t band1 = tmem + (FP4 ? T::kBand8 + 40 : DT == 1 ? T::kBand8 : T::kBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -1005,15 +1011,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         const OpDesc hop{hop0.d128 + hoff, hop0.d32 + hoff};
         const uint32_t d2 = tmem + T::kD2Base + reg * T::kD2Cols;
         const int rj = tile_rule<BATCH>(p, first, j).r;
-        if constexpr (FP4) {
-          // S = band x (H & 15) + band x (H - (H & 15)), both e4m3 halves of
-          // the H buffer, the second only when H can exceed 15
-          band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
-          if (2 * rj + 1 > 15) {
-            constexpr uint64_t kHi = (uint64_t)((kTile * kWin) >> 4);
-            band_mma<1, kTile, 1, true>(d2, band8, OpDesc{hop.d128 + kHi, hop.d32 + kHi}, idesc2);
-          }
-        } else if constexpr (DEC) {
+        if constexpr (DEC) {
           // S = band x (H & 15) + (16 band) x (H >> 4), the second only when H
           // can exceed 15; both e4m3 halves of the H buffer
           band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
@@ -1120,29 +1118,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           if (c == 4 && !last) break;
-          if constexpr (FP4) {
-            // D1 holds 0.5 H (e2m1 products), and 0.5 H * 2 + 1024 is exactly
-            // 1024 + H, an f16 whose low byte is H.  e4m3 digits: lo = H & 15,
-            // the code of itself times 2^-9, and hi = H - lo (0, 16 or 32:
-            // codes 0x10 and 0x18, the e4m3 numbers 16 * 2^-9 and 32 * 2^-9)
-            const __half2 k2 = __float2half2_rn(2.0f), k1024 = __float2half2_rn(1024.0f);
-            uint32_t e[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k2, k1024)),
-                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k2, k1024)), 0x6420);
-            *reinterpret_cast<uint4 *>(hop + off8[c]) =
-                make_uint4(e[0] & 0x0F0F0F0Fu, e[1] & 0x0F0F0F0Fu, e[2] & 0x0F0F0F0Fu, e[3] & 0x0F0F0F0Fu);
-            if (split) {
-              uint32_t hi[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const uint32_t t = e[i] & 0x30303030u;
-                hi[i] = t - ((t >> 2) & 0x08080808u);
-              }
-              *reinterpret_cast<uint4 *>(hop + kTile * kWin + off8[c]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            }
-          } else if constexpr (DEC) {
+          if constexpr (DEC) {
             // e4m3 digits H & 15 and H >> 4 (at most 4): each the code of
             // itself times 2^-9 (e4m3 subnormals for 1..7)
             const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
@@ -1164,13 +1140,14 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
             *reinterpret_cast<uint4 *>(hop + off16b[c]) = make_uint4(v[c][4], v[c][5], v[c][6], v[c][7]);
           } else {
             // the e4m3 code of k * 2^-9 is k itself for k <= 15, and k * 2^-9 *
-            // 512 + 1024 is exactly 1024 + k, an f16 whose low byte is k
-            const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
+            // 512 + 1024 is exactly 1024 + k, an f16 whose low byte is k (FP4:
+            // D1 holds 0.5 k, the e2m1 products, and 0.5 k * 2 + 1024 = 1024 + k)
+            const __half2 ks = __float2half2_rn(FP4 ? 2.0f : 512.0f), k1024 = __float2half2_rn(1024.0f);
             uint32_t e[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k512, k1024)),
-                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k512, k1024)), 0x6420);
+              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), ks, k1024)),
+                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), ks, k1024)), 0x6420);
             *reinterpret_cast<uint4 *>(hop + off8[c]) = make_uint4(e[0], e[1], e[2], e[3]);
           }
         }
@@ -1413,8 +1390,8 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_bits_kernel(const __grid_cons
   ltl_tc_body<1, true, false, false, true, false>(p);
 }
 
-// FP4 (e2m1) pass-1 operands on the re-encoded window, pass 2 on e4m3 digits:
-// uint8, one-bit and four-bit storage.
+// FP4 (e2m1) pass-1 operands on the re-encoded window, pass 2 as in the FP8
+// kernel (e4m3 for 2r+1 <= 15, else f16): uint8, one-bit and four-bit storage.
 __global__ void __launch_bounds__(kThreads, 1) ltl_fp4_kernel(const __grid_constant__ TcParams p) {
   ltl_tc_body<1, true, false, false, false, false, false, false, true>(p);
 }

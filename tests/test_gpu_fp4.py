@@ -5,10 +5,10 @@ The window is re-encoded in shared memory as e2m1 (a state-1 cell is code 1 =
 first 8 bytes of every 16-byte unit) and multiplied by an e2m1 band of ones
 held in tensor memory (one element per byte, code in bits 2..5), so pass 1
 gives H / 2 exactly.  H <= 33 is not an e2m1 number (the largest is 6), so
-the convert warps split it into two e4m3 digits, H & 15 and H - (H & 15), and
-pass 2 adds both against the e4m3 band of ones: the e2m1 / e4m3 mix of
-kind::f8f6f4 (Sec. VI names lower precisions; Sec. V-A argues exactness for
-FP16, which the digit split carries over).  Every storage the FP4 kernel
+pass 2 is the FP8 kernel's: H as e4m3 against the e4m3 band of ones when
+2r+1 <= 15 (the e2m1 / e4m3 mix of kind::f8f6f4), else the f16 values H / 2
+against an f16 band of 2^-8 (Sec. VI names lower precisions; Sec. V-A argues
+exactness for FP16, which both operand sets keep).  Every storage the FP4 kernel
 serves (uint8, one bit, four bits per cell) is checked: box counts at every
 radius, all-ones and impulse grids (H = 33 and S = 1089 at r = 16), whole
 steps of the scaled rules and of the paper's Table IV, multi-state decay,
@@ -257,4 +257,32 @@ def test_batch_step_steps_fp4_instances_one_by_one(cat):
             assert_same(g.get_state(), oracle.step(host, orule(rl), n_steps=3), f"batched r={rl['r']}")
     finally:
         for g in gs:
+            g.close()
+
+
+def test_auto_dtype_takes_fp4_on_four_bit_storage(cat):
+    """CAT_DTYPE_AUTO: FP4 operands on four-bit storage (two-state and
+    multi-state rules), FP8 on uint8 and one-bit storage; the chosen operands
+    step like the oracle."""
+    cases = [(inputs.scaled_rule(12, M=1), cat.STORE_NIB4, cat.DTYPE_FP4_E2M1),
+             (dict(inputs.MULTISTATE_R10_C16), cat.STORE_NIB4, cat.DTYPE_FP4_E2M1),
+             (dict(r=3, C=5, M=0, s1=10, s2=30, b1=12, b2=25), cat.STORE_NIB4, cat.DTYPE_FP4_E2M1),
+             (inputs.scaled_rule(12, M=1), cat.STORE_U8, cat.DTYPE_FP8_E4M3),
+             (dict(inputs.MULTISTATE_R10_C16), cat.STORE_U8, cat.DTYPE_FP8_E4M3),
+             (inputs.scaled_rule(12, M=1), cat.STORE_BIT1, cat.DTYPE_FP8_E4M3)]
+    for i, (rule, storage, want_dtype) in enumerate(cases):
+        H, W = 210 + 13 * i, 333 - 17 * i
+        if rule["C"] > 2:
+            host = (inputs.uniform_states(H, W, rule["C"], 90 + i) * (inputs.bernoulli(H, W, 0.3, 95 + i) == 0)
+                    + inputs.bernoulli(H, W, 0.3, 95 + i)).astype(np.uint8) % rule["C"]
+        else:
+            host = inputs.bernoulli(H, W, 0.5, 90 + i)
+        g = cat.Grid(H, W, rule, kernel="tcgen05", dtype="auto", storage=storage)
+        try:
+            assert cat.cat_get_options(g.handle)["dtype"] == want_dtype, (rule, storage)
+            g.set_state(host)
+            g.step(3)
+            assert g.status() == cat.CAT_OK
+            assert_same(g.get_state(), oracle.step(host, orule(rule), n_steps=3), f"auto dtype case {i}")
+        finally:
             g.close()
