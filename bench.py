@@ -663,9 +663,12 @@ def run_cat(args, rank, world, local):
         group_ms.setdefault(kname, []).append(a.elapsed_time(b) / cnt)
     kernel_launch_ms = {k: statistics.mean(v) for k, v in group_ms.items()}   # average launch, live
     avg_launch_ms = sum(kernel_launch_ms[kern_of[r]] for r in RADII) / len(RADII)
-    # per radius (after the timed region): each launch between its own events
+    # per radius (after the timed region): each launch between its own events,
+    # behind one untimed launch so that the first event is not recorded on an
+    # idle device ahead of the host's launch call
     per_r = {}
     for r in RADII:
+        grids[r].step(1, stream)
         t = time_launches(torch, lambda: grids[r].step(1, stream), 3, stream)
         per_r[r] = statistics.mean(t)
 
@@ -844,7 +847,7 @@ def run_cat(args, rank, world, local):
             "tensor_peaks_tflops": tensor_peaks,
             "roofline_whole_sweep": roof(value / world, 2.0, tpeak, hbm),
             "per_r_cell_updates_per_s": per_r_rate,
-            "per_r_source": "after the timed region: three launches per radius, each between its own CUDA events",
+            "per_r_source": "after the timed region: one untimed launch, then three launches per radius, each between its own CUDA events",
             "comparators_cell_updates_per_s": {k: {str(r): v for r, v in row.items()} for k, row in comps.items()},
             "comparators_roofline_frac": comp_roofs,
             # the headline kernel's rate over the fastest CUDA-core kernel (direct
