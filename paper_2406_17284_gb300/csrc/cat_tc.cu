@@ -195,10 +195,11 @@ struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
   static constexpr int NS = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
   static constexpr int NR = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
-  static constexpr int NE = BITS ? 3 : (ENC ? 2 : 1);        // encoded windows (encode one ahead)
-  // pass-2 operand buffers (FP16: one, so that its two 50 KiB encoded
-  // windows fit; the encode then runs beside pass 1 instead of before it)
-  static constexpr int NH = SW ? 3 : (DT == 0 ? 1 : 2);
+  static constexpr int NE = (BITS || NIB) ? 3 : (ENC ? 2 : 1);  // encoded windows (encode ahead)
+  // pass-2 operand buffers: FP16 one, so that its two 50 KiB encoded windows
+  // fit (the encode then runs beside pass 1 instead of before it); four-bit
+  // storage one, for its third encoded window (measured 2% faster)
+  static constexpr int NH = SW ? 3 : ((DT == 0 || NIB) ? 1 : 2);
   static constexpr uint32_t kXs = 0;                          // raw windows (TMA)
   static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : NIB ? 96 * kWin : kWin * Geo<SW>::kRows;  // one window load
   static constexpr uint32_t kXsStride = (kXsBytes + 1023) / 1024 * 1024;  // 128B-swizzle atoms stay aligned
