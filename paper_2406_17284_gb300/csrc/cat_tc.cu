@@ -315,13 +315,12 @@ __device__ __forceinline__ void encode_window(const uint8_t *xs, uint8_t *xe, bo
   }
 }
 
-// Four cells' bits (bits 0..3 of n) -> four bytes 0/1 (no carries: the four
-// shifted copies of n land on disjoint bit ranges).
-__device__ __forceinline__ uint32_t bits4_to_bytes(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
-
 // Unpacks a bit-packed window stage (160 rows of 48 bytes, window cell x' at
-// bit x' + 112 of the row) into the e4m3 window operand: 0x01 for a live cell
-// (FP4: e2m1 units, code 1 for a live cell).  One item is half a row (80
+// bit x' + 112 of the row) into the e4m3 window operand: byte x' is the cell's
+// bit left in place within its nibble, 2^(x' mod 4) (codes 1, 2, 4, 8: the
+// e4m3 numbers 2^(x' mod 4) * 2^-9) for a live cell, which the pass-1 band's
+// 2^-(x' mod 4) scales back to 2^-9 exactly -- one byte permute and one mask
+// per four cells (FP4: e2m1 units, code 1 for a live cell).  One item is half a row (80
 // cells, 16-cell chunks 5h .. 5h+4): three aligned 32-bit loads (bytes 12 +
 // 12h ..), shifted by 16 bits for h = 0 so that the chunks are the five
 // consecutive 16-bit fields.
@@ -342,9 +341,10 @@ __device__ __forceinline__ void unpack_window(const uint8_t *xs, uint8_t *xe, in
       if constexpr (FP4)
         *reinterpret_cast<uint2 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
             make_uint2(bits8_to_nibbles(f[i]), bits8_to_nibbles(f[i] >> 8));
-      else
+      else   // byte j of each word: bit j of its cell's source nibble, i.e. 2^j for a live cell
         *reinterpret_cast<uint4 *>(xe + op_off(kWin, 1, row, 16 * (5 * h + i))) =
-            make_uint4(bits4_to_bytes(f[i]), bits4_to_bytes(f[i] >> 4), bits4_to_bytes(f[i] >> 8), bits4_to_bytes(f[i] >> 12));
+            make_uint4(__byte_perm(f[i], 0, 0x0000) & 0x08040201u, __byte_perm(f[i] >> 4, 0, 0x0000) & 0x08040201u,
+                       __byte_perm(f[i], 0, 0x1111) & 0x08040201u, __byte_perm(f[i] >> 4, 0, 0x1111) & 0x08040201u);
     }
   }
 }
@@ -405,10 +405,11 @@ __device__ __forceinline__ uint32_t bytes_to_nib_pairs(uint32_t w) { return w | 
 // one with 2^-8 for one (its pass 1 leaves H / 2, not H * 2^-9), and an e2m1
 // band for pass 1 in the 40 columns after the e4m3 one (kind::f8f6f4 reads an
 // e2m1 A operand from tensor memory as one element per byte with the code in
-// bits 2..5, so 1.0 = 0010b is 0x08), all with offset 16.  Convert warp
-// (q, kq) writes lanes 32q .. 32q+31 and every other 8-column chunk from
-// chunk kq.
-template <int DT, bool SW, bool WIDE = false, bool FP4 = false>
+// bits 2..5, so 1.0 = 0010b is 0x08), all with offset 16.  The one-bit FP8
+// kernel keeps its pass-1 band in those 40 columns too: 2^-(k mod 4) at K
+// index k, against window bytes 2^(k mod 4) * 2^-9.  Convert warp (q, kq)
+// writes lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
+template <int DT, bool SW, bool WIDE = false, bool FP4 = false, bool BITS = false>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
   using G = Geo<SW, WIDE>;
   using T = Tm<DT, SW, WIDE>;
@@ -417,9 +418,11 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
   // one) and the e4m3 band, or in the short window the e4m3 bands of pass 1
   // and pass 2, or in the wide tile the e4m3 band and the band of 16s (offset
   // 32, rows 96..127 zero), or in the FP4 kernel the f16 band of 2^-8 (pass 2
-  // on H / 2), the e4m3 band and the e2m1 band (pass 1, after the e4m3 one)
+  // on H / 2), the e4m3 band and the e2m1 band (pass 1, after the e4m3 one);
+  // the one-bit kernel's pass-1 band sits there too: e4m3 2^-(k mod 4) at
+  // column k, against window bytes 2^(k mod 4) * 2^-9 for live cells
   constexpr int n0 = WIDE ? 5 : (SW ? 5 : 10), n1 = WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
-  constexpr int n = FP4 ? 20 : n1;
+  constexpr int n = (FP4 || BITS) ? 20 : n1;
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
   for (int c = kq; c < n; c += 2) {                 // warp-uniform
@@ -447,7 +450,8 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int d = k0 + b - m;
-          if (d >= off - r && d <= off + r) w |= one8 << (8 * b);
+          const uint32_t v8 = (third && !FP4) ? 0x38u - 8u * (uint32_t)b : one8;   // 1, 1/2, 1/4, 1/8
+          if (d >= off - r && d <= off + r) w |= v8 << (8 * b);
         }
       }
       v[i] = w;
@@ -881,7 +885,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       // up to 1089 * scale, which f16 represents exactly
       // (FP4: e2m1 window and band, the band after the e4m3 one)
       const uint32_t idesc1 = idesc_f16acc(128, G::kRows) | (FP4 ? kIdescE2M1 : 0u);
-      const uint32_t band1 = tmem + (FP4 ? T::kBand8 + 40 : DT == 1 ? T::kBand8 : T::kBand16);
+      const uint32_t band1 = tmem + ((FP4 || BITS) ? T::kBand8 + 40 : DT == 1 ? T::kBand8 : T::kBand16);
       const OpDesc win0 = op_descs(s_base + (ENC ? L::kXe : L::kXs));
       bool ok = true;
       if (p.inject == 1) {  // timeout test: nobody ever arrives on `never`
@@ -1055,7 +1059,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
     // the bands for the first tile
-    store_bands<DT, SW, WIDE, FP4>(tmem, r0, q, kq, lane);
+    store_bands<DT, SW, WIDE, FP4, BITS>(tmem, r0, q, kq, lane);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -1091,7 +1095,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           if (!ok) break;
         }
         tc_fence_after();
-        store_bands<DT, SW, WIDE, FP4>(tmem, rj, q, kq, lane);
+        store_bands<DT, SW, WIDE, FP4, BITS>(tmem, rj, q, kq, lane);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
