@@ -55,8 +55,9 @@ extern "C" {
  *   r      neighbourhood radius, 1 <= r <= 32.  Up to 16 (the fragment size,
  *          Sec. IV-A) every kernel serves it; 17..32 (the extension to a
  *          second halo fragment that Sec. VII describes) is served with uint8
- *          storage and the zero boundary by TCGEN05 on 96 x 96 tiles (FP8,
- *          C = 2, Moore; CAT_KERNEL_AUTO picks it), by the FP16 fragment
+ *          storage and the zero boundary by TCGEN05 on 128 x 128 tiles in a
+ *          192 x 192 window or 96 x 96 tiles in a 160 x 160 one (FP8, C = 2,
+ *          Moore; CAT_KERNEL_AUTO picks the first), by the FP16 fragment
  *          kernel (MMA_SYNC, Moore, every C) and by the stencil.
  *   C      number of states, 2 <= C <= 255
  *   M      1: the centre cell counts towards k; 0: it does not
@@ -88,8 +89,8 @@ enum { CAT_BOUNDARY_ZERO = 0, CAT_BOUNDARY_PERIODIC = 1 };
  *   FP8_E4M3  a state byte 0x01 read as e4m3 is 2^-9, so the raw bytes are the
  *             pass-1 operand; H * 2^-9 is an e4m3 number while H <= 15
  *             (2r+1 <= 15).  Beyond that the TCGEN05 kernel passes H to the
- *             second product as f16 operands on 128 x 128 tiles, and on the
- *             96 x 96 tile (H <= 65) as two e4m3 digits, H & 15 against the
+ *             second product as f16 operands in the 160-row window, and with
+ *             a 32-cell halo (H <= 65) as two e4m3 digits, H & 15 against the
  *             band and H >> 4 against a band of 16s (f32 accumulation).
  *   INT8      H <= 65 < 127; served by MMA_SYNC (sm_103a has no tcgen05 kind::i8).
  *   FP4_E2M1  TCGEN05, Moore, r <= 16, one step per launch, uint8 / one-bit /
@@ -132,8 +133,8 @@ enum {
 enum { CAT_STORE_U8 = 0, CAT_STORE_BIT1 = 1, CAT_STORE_NIB4 = 2 };
 
 /* Which kernel advances the grid.
- *   TCGEN05   TMA-staged haloed 128x128 tiles (96x96 with a 32-cell halo for
- *             r > 16), both band products on the 5th-generation tensor cores
+ *   TCGEN05   TMA-staged haloed 128x128 tiles (a 32-cell halo for r > 16, or
+ *             96x96 tiles), both band products on the 5th-generation tensor cores
  *             (tcgen05.mma, TMEM accumulators), transition fused into the
  *             epilogue (FP16 or FP8 operands).
  *   MMA_SYNC  the paper's own fragment scheme (Alg. 1: three 16x16 band
@@ -220,14 +221,17 @@ CAT_API int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32
 
 /* Tile shape and window of the TCGEN05 Moore kernel (the ty, tx tile options;
  * the step's results do not depend on them, only its speed).
- *   ty x tx  0 x 0: chosen by the radius (128 x 128 for r <= 16, else 96 x 96);
- *            128 x 128: the tile of a 160 x 160 window with a 16-cell halo
- *            (r <= 16); 96 x 96: the tile of the same window with a 32-cell
+ *   ty x tx  0 x 0 or 128 x 128: the 128 x 128 tile (its window chosen
+ *            below); 96 x 96: the tile of a 160 x 160 window with a 32-cell
  *            halo (any r <= 32; FP8 operands, C = 2, uint8 storage, the zero
  *            boundary, one step per launch).
- *   window_rows  0: chosen by the rule (144 for FP8 operands, C = 2, r <= 7,
- *            else 160); 144: the short window (128 x 128 tile, FP8, C = 2,
- *            r <= 7, uint8 storage); 160: the full window.
+ *   window_rows  0: chosen by the rule (144 for FP8 operands, C = 2, r <= 7;
+ *            192 for r > 16; else 160); 144: the short window (FP8, C = 2,
+ *            r <= 7, uint8 storage); 160: the 160 x 160 window with a
+ *            16-cell halo (r <= 16); 192: the 192 x 192 window with a 32-cell
+ *            halo (any r <= 32; FP8 operands, C = 2, uint8 storage, the zero
+ *            boundary, one step per launch; pass 2 on two e4m3 digits of H
+ *            into f32).
  * The autotuner (cat_autotune) drives this call.  Later changes of
  * kernel, dtype or storage that a chosen tile does not serve are rejected by
  * cat_set_options.  Errors: INVALID_ARG (other shapes), UNSUPPORTED (a shape
@@ -236,8 +240,8 @@ CAT_API int cat_set_tile(cat_handle_t h, int32_t ty, int32_t tx, int32_t window_
 
 /* The options in force: kernel, operand dtype (CAT_DTYPE_AUTO for kernels
  * without one), storage, steps per launch, and for the TCGEN05 Moore kernel
- * the tile side (128 or 96) and window rows (144 or 160; 0 for the 96 x 96
- * tile); 0 where they do not apply.  Any pointer may be NULL.  Errors:
+ * the tile side (128 or 96) and window rows (144, 160 or 192; 0 for the
+ * 96 x 96 tile); 0 where they do not apply.  Any pointer may be NULL.  Errors:
  * INVALID_ARG (NULL handle).                                                */
 CAT_API int cat_get_options(cat_handle_t h, int32_t *kernel, int32_t *dtype, int32_t *storage,
                             int32_t *steps_per_launch, int32_t *tile, int32_t *window_rows);

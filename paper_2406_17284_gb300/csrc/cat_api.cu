@@ -91,7 +91,7 @@ struct cat_instance {
   // per buffer: window boxes 128 x 160 and 32 x 160, the 128 x 128 tile box,
   // the window boxes of the short-window kernel, 128 x 144 and 32 x 144, and
   // the 96 x 96 tile box (no swizzle) of the wide-tile kernel
-  CUtensorMap maps[2][6];
+  CUtensorMap maps[2][8];
   int32_t tile = 0;     // cat_set_tile: 0 chosen by the radius, 128 or 96
   int32_t window = 0;   // cat_set_tile: 0 chosen by the rule, 144 or 160
   DeviceInfo dev;
@@ -158,7 +158,7 @@ int build_maps(cat_instance *h) {
       const int64_t wb = (h->W + 1) / 2;
       if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, wb, h->pitch, 96, 160, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
       if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, wb, h->pitch, 64, 128, CU_TENSOR_MAP_SWIZZLE_64B))) return rc;
-      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][0];
+      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][6] = h->maps[b][7] = h->maps[b][0];
     }
     return CAT_OK;
   }
@@ -168,7 +168,7 @@ int build_maps(cat_instance *h) {
       const int64_t wb = (h->W + 7) / 8;
       if ((rc = make_map(&h->maps[b][0], h->buf[b], h->H, wb, h->pitch, 48, 160, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
       if ((rc = make_map(&h->maps[b][2], h->buf[b], h->H, wb, h->pitch, 16, 128, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
-      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][0];
+      h->maps[b][1] = h->maps[b][3] = h->maps[b][4] = h->maps[b][5] = h->maps[b][6] = h->maps[b][7] = h->maps[b][0];
     }
     return CAT_OK;
   }
@@ -182,15 +182,21 @@ int build_maps(cat_instance *h) {
     if ((rc = make_map(&h->maps[b][3], h->buf[b], H, W, h->pitch, 128, 144, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
     if ((rc = make_map(&h->maps[b][4], h->buf[b], H, W, h->pitch, 32, 144, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
     if ((rc = make_map(&h->maps[b][5], h->buf[b], H, W, h->pitch, 96, 96, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = make_map(&h->maps[b][6], h->buf[b], H, W, h->pitch, 128, 192, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = make_map(&h->maps[b][7], h->buf[b], H, W, h->pitch, 32, 192, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
   }
   return CAT_OK;
 }
 
-// The wide-tile kernel (96 x 96 tiles, a 32-cell halo) serves radii above 16
-// on tcgen05, and any radius when cat_set_tile asks for it.
+// The kernels with a 32-cell halo serve radii above 16 on tcgen05, and any
+// radius when cat_set_tile asks for one of them: the 128 x 128 tile in a
+// 192 x 192 window (radii above 16 by default, or window 192), or the
+// 96 x 96 tile in the 160 x 160 window (tile 96).
 bool wide_tile(const cat_instance *h) {
-  return h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' && (h->rule.r > 16 || h->tile == 96);
+  return h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' &&
+         (h->rule.r > 16 || h->tile == 96 || h->window == 192);
 }
+bool big_window(const cat_instance *h) { return wide_tile(h) && h->tile != 96; }
 
 // The short-window kernel serves FP8 operands on two-state rules with r <= 7
 // (pass 2 then runs on e4m3, and 128 + 2r window rows fit in 144), unless
@@ -218,8 +224,9 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     const bool nib = h->storage == CAT_STORE_NIB4;
     const bool sw = !vn && !bits && !nib && short_window(h);
     const bool wide = !vn && wide_tile(h);
-    p.map_in_a = h->maps[in][sw ? 3 : 0];
-    p.map_in_b = h->maps[in][sw ? 4 : 1];
+    const bool big = wide && big_window(h);   // 128 x 128 tiles in the 192 x 192 window
+    p.map_in_a = h->maps[in][big ? 6 : sw ? 3 : 0];
+    p.map_in_b = h->maps[in][big ? 7 : sw ? 4 : 1];
     p.map_out = h->maps[1 - in][2];
     p.map_ctr = h->maps[in][2];
     p.n_steps = n_steps;
@@ -231,8 +238,8 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
       p.gbar = reinterpret_cast<uint32_t *>(h->d_err) + 1;
       p.gbar_base = h->gbar_count;
     }
-    const int ts = wide ? 96 : 128;
-    if (wide) {   // 96 x 96 centre and output tiles
+    const int ts = wide && !big ? 96 : 128;
+    if (wide && !big) {   // 96 x 96 centre and output tiles
       p.map_out = h->maps[1 - in][5];
       p.map_ctr = h->maps[in][5];
     }
@@ -249,6 +256,7 @@ int launch_step(cat_instance *h, int in, int32_t *sums, int64_t sums_ld, cudaStr
     const int grid = p.n_tiles < h->dev.sms ? p.n_tiles : h->dev.sms;
     const bool fp4 = h->dtype == CAT_DTYPE_FP4_E2M1;
     e = vn ? cat::vn_launch(p, grid, s)
+           : big  ? cat::big_launch(p, grid, s)
            : wide ? cat::wide_launch(p, grid, s)
            : fp4  ? cat::fp4_launch(p, bits ? 1 : nib ? 2 : 0, grid, s)
            : nib  ? cat::nib_launch(p, grid, s)
@@ -635,6 +643,7 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
            : storage == CAT_STORE_BIT1 && h->rule.r <= 5 && h->rule.C == 2 ? CAT_KERNEL_BITSLICE
                                                                           : CAT_KERNEL_TCGEN05;
   const int32_t cur_tile = tuned_tile >= 0 ? 0 : h->tile;   // a cached choice brings its own tile
+  const int32_t cur_window = tuned_tile >= 0 ? 0 : h->window;
   // AUTO: FP8 on tcgen05 (FP4 on four-bit storage, whose state-1 nibble
   // flags are the e2m1 operand as they stand: measured faster at every radius
   // and state count), FP16 on the fragment kernel
@@ -645,7 +654,7 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
   if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_INT8)
     return fail(CAT_ERR_UNSUPPORTED, "sm_103a has no tcgen05 kind::i8; INT8 runs on CAT_KERNEL_MMA_SYNC");
   if (kernel == CAT_KERNEL_TCGEN05 && dtype == CAT_DTYPE_FP4_E2M1 &&
-      (vn || wide || cur_tile == 96 || steps_per_launch > 1))
+      (vn || wide || cur_tile == 96 || cur_window == 192 || steps_per_launch > 1))
     return fail(CAT_ERR_UNSUPPORTED, "FP4 operands are served by the 128 x 128 tcgen05 Moore kernel (r <= 16), "
                                      "one step per launch");
   if (kernel == CAT_KERNEL_MMA_SYNC && dtype != CAT_DTYPE_FP16 && dtype != CAT_DTYPE_INT8)
@@ -659,11 +668,13 @@ int cat_set_options(cat_handle_t h, int32_t kernel, int32_t dtype, int32_t stora
                                        "the zero boundary and r <= 5");
     dtype = CAT_DTYPE_AUTO;
   }
-  // the 96 x 96 tile: radii above 16 on tcgen05, or any radius after cat_set_tile(96, 96)
-  const bool wide_tc = kernel == CAT_KERNEL_TCGEN05 && !vn && (wide || cur_tile == 96);
+  // the 32-cell-halo kernels: radii above 16 on tcgen05, or any radius after
+  // cat_set_tile(96, 96) or a 192-row window
+  const bool wide_tc = kernel == CAT_KERNEL_TCGEN05 && !vn && (wide || cur_tile == 96 || cur_window == 192);
   if (wide_tc && (dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2 || storage != CAT_STORE_U8 || steps_per_launch > 1))
     return fail(CAT_ERR_UNSUPPORTED,
-                "the 96 x 96 tcgen05 tile (r > 16) serves FP8 operands, two-state rules, uint8 storage, one step per launch");
+                "the tcgen05 kernels for r > 16 (192-row window, 96 x 96 tile) serve FP8 operands, two-state rules, "
+                "uint8 storage, one step per launch");
   if (wide && kernel == CAT_KERNEL_TCGEN05 && vn)
     return fail(CAT_ERR_UNSUPPORTED, "the simplified von Neumann cross with r > 16 is served by the stencil");
   if (wide && kernel == CAT_KERNEL_MMA_SYNC && (dtype != CAT_DTYPE_FP16 || vn))
@@ -723,9 +734,9 @@ int cat_get_options(cat_handle_t h, int32_t *kernel, int32_t *dtype, int32_t *st
   if (dtype) *dtype = h->dtype;
   if (storage) *storage = h->storage;
   if (steps_per_launch) *steps_per_launch = h->steps_per_launch;
-  if (tile) *tile = h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' ? (wide_tile(h) ? 96 : 128) : 0;
-  if (window_rows) *window_rows = h->kernel != CAT_KERNEL_TCGEN05 || h->rule.nbhd != 'M' || wide_tile(h) ? 0
-                                  : short_window(h) ? 144 : 160;
+  if (tile) *tile = h->kernel == CAT_KERNEL_TCGEN05 && h->rule.nbhd == 'M' ? (wide_tile(h) && !big_window(h) ? 96 : 128) : 0;
+  if (window_rows) *window_rows = h->kernel != CAT_KERNEL_TCGEN05 || h->rule.nbhd != 'M' ? 0
+                                  : big_window(h) ? 192 : wide_tile(h) ? 0 : short_window(h) ? 144 : 160;
   return CAT_OK;
 }
 
@@ -733,10 +744,15 @@ int cat_set_tile(cat_handle_t h, int32_t ty, int32_t tx, int32_t window_rows) {
   if (!h) return fail(CAT_ERR_INVALID_ARG, "handle is NULL");
   const bool t0 = ty == 0 && tx == 0, t128 = ty == 128 && tx == 128, t96 = ty == 96 && tx == 96;
   if (!t0 && !t128 && !t96) return fail(CAT_ERR_INVALID_ARG, "tile %d x %d: choose 0 x 0, 128 x 128 or 96 x 96", ty, tx);
-  if (window_rows != 0 && window_rows != 144 && window_rows != 160)
-    return fail(CAT_ERR_INVALID_ARG, "window of %d rows: choose 0, 144 or 160", window_rows);
+  if (window_rows != 0 && window_rows != 144 && window_rows != 160 && window_rows != 192)
+    return fail(CAT_ERR_INVALID_ARG, "window of %d rows: choose 0, 144, 160 or 192", window_rows);
   const bool vn = h->rule.nbhd == 'N';
-  if (t128 && h->rule.r > 16) return fail(CAT_ERR_UNSUPPORTED, "the 128 x 128 tile serves radii up to 16");
+  if (window_rows == 160 && !t96 && h->rule.r > 16)
+    return fail(CAT_ERR_UNSUPPORTED, "the 160-row window serves radii up to 16 on the 128 x 128 tile");
+  if (window_rows == 192 && (t96 || h->kernel != CAT_KERNEL_TCGEN05 || vn || h->dtype != CAT_DTYPE_FP8_E4M3 ||
+                             h->rule.C != 2 || h->storage != CAT_STORE_U8 || h->ghost || h->steps_per_launch > 1))
+    return fail(CAT_ERR_UNSUPPORTED, "the 192-row window serves the 128 x 128 tcgen05 Moore kernel with FP8 operands, "
+                                     "two-state rules, uint8 storage, the zero boundary and one step per launch");
   if (t96 && (h->kernel != CAT_KERNEL_TCGEN05 || vn || h->dtype != CAT_DTYPE_FP8_E4M3 || h->rule.C != 2 ||
               h->storage != CAT_STORE_U8 || h->ghost || h->steps_per_launch > 1))
     return fail(CAT_ERR_UNSUPPORTED, "the 96 x 96 tile serves the tcgen05 Moore kernel with FP8 operands, two-state "

@@ -95,7 +95,11 @@ cudaError_t vn_launch(const TcParams &p, int grid, cudaStream_t s);
 // instance): map_in_a / map_in_b the 128 x 160 and 32 x 160 window maps,
 // map_ctr / map_out the 96 x 96 tile maps; tiles_x, n_tiles in 96 x 96 tiles.
 cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s);
-// FP4 (e2m1) pass-1 operands, pass 2 on e4m3 digits, on the re-encoded window
+// The 128 x 128 tile in a 192 x 192 window (32-cell halo), radii up to 32
+// (FP8, C = 2, single instance): map_in_a / map_in_b the 128 x 192 and
+// 32 x 192 window maps, map_ctr / map_out the 128 x 128 tile maps.
+cudaError_t big_launch(const TcParams &p, int grid, cudaStream_t s);
+// FP4 (e2m1) pass-1 operands, pass 2 as in the FP8 kernel, on the re-encoded window
 // of uint8 (storage 0), one-bit (1) or four-bit (2) grids: the maps of the
 // FP8 kernel for that storage.
 cudaError_t fp4_launch(const TcParams &p, int storage, int grid, cudaStream_t s);

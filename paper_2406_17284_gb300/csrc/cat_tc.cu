@@ -81,17 +81,23 @@ constexpr int kMaxRegions = 3;
 // (96 + 2 * 32 = 160; x0 - 32 stays 16-byte aligned since x0 is a multiple of
 // 96).  The bands have offset 32 and rows 96..127 zero, so the MMA shapes stay
 // M = 128, K = 160; pass 2 has N = 96.
-template <bool SW, bool WIDE = false>
+// Big window (BIG, radii up to 32 on the 128 x 128 tile): the window is
+// 192 x 192 starting 32 cells above and left of the tile, so pass 1 has
+// N = K = 192 (six K-steps); pass 2 takes H as two e4m3 digits (H <= 65)
+// against the band of ones and a band of 16s (48 columns each at K = 192)
+// into an f32 accumulator over the tile's own D1 region: 2 * 192 + 48 + 48 =
+// 480 columns.
+template <bool SW, bool WIDE = false, bool BIG = false>
 struct Geo {
   static constexpr int kTS = WIDE ? 96 : 128;         // output tile side
-  static constexpr int kXOff = WIDE ? 32 : 16;        // window columns left of the tile
-  static constexpr int kRows = SW ? 144 : 160;        // window rows = pass-1 N
-  static constexpr int kYOff = WIDE ? 32 : (SW ? 8 : 16);   // window rows above the tile
+  static constexpr int kXOff = (WIDE || BIG) ? 32 : 16;   // window columns left of the tile
+  static constexpr int kRows = SW ? 144 : BIG ? 192 : 160;   // window rows = pass-1 N
+  static constexpr int kYOff = (WIDE || BIG) ? 32 : (SW ? 8 : 16);   // window rows above the tile
   static constexpr int kRegions = SW ? 3 : 2;
-  static constexpr int kRegionCols = SW ? 144 : 160;
+  static constexpr int kRegionCols = SW ? 144 : BIG ? 192 : 160;
   static constexpr uint32_t kBand16 = 320;            // f16 band (standard only)
-  static constexpr uint32_t kBand8 = SW ? 432 : 416;  // e4m3 band, offset 16 (pass 1; also pass 2 if standard)
-  static constexpr uint32_t kBand8P2 = SW ? 472 : 416;  // e4m3 band for pass 2 (offset kYOff)
+  static constexpr uint32_t kBand8 = SW ? 432 : BIG ? 384 : 416;  // e4m3 band, offset kXOff (pass 1; also pass 2 if not SW)
+  static constexpr uint32_t kBand8P2 = SW ? 472 : BIG ? 384 : 416;  // e4m3 band for pass 2 (offset kYOff)
 };
 constexpr uint32_t kTmemCols = 512;
 
@@ -109,19 +115,21 @@ constexpr uint32_t kTmemCols = 512;
 // no f16 band, and separate D1 / D2 regions, 2 + 1 or 1 + 2 -- measured 8%
 // and 3% slower at r >= 8 than the shared regions, 2.05 and 2.15 against
 // 2.22 * 10^12 cell updates/s, so it is not used there.)
-template <int DT, bool SW, bool WIDE = false>
+template <int DT, bool SW, bool WIDE = false, bool BIG = false>
 struct Tm {
+  using GB = Geo<SW, false, BIG>;
   static constexpr bool kDec = DT == 1 && !SW && WIDE;
-  static constexpr int kND1 = kDec ? 2 : Geo<SW>::kRegions;
-  static constexpr int kND2 = kDec ? 1 : Geo<SW>::kRegions;
-  static constexpr uint32_t kD1Cols = Geo<SW>::kRegionCols;
+  static constexpr int kND1 = kDec ? 2 : GB::kRegions;
+  static constexpr int kND2 = kDec ? 1 : GB::kRegions;
+  static constexpr uint32_t kD1Cols = GB::kRegionCols;
   static constexpr uint32_t kD2Base = kDec ? kND1 * kD1Cols : 0;
-  static constexpr uint32_t kD2Cols = kDec ? Geo<SW, WIDE>::kTS : Geo<SW>::kRegionCols;
-  static constexpr uint32_t kBand16 = Geo<SW>::kBand16;     // FP16 kernel only
-  static constexpr uint32_t kBand8 = kDec ? kD2Base + kND2 * kD2Cols : Geo<SW>::kBand8;
-  static constexpr uint32_t kBand8P2 = kDec ? kBand8 : Geo<SW>::kBand8P2;
-  static constexpr uint32_t kBand8x16 = kBand8 + 40;        // wide tile: the band of 16s
+  static constexpr uint32_t kD2Cols = kDec ? Geo<SW, WIDE>::kTS : GB::kRegionCols;
+  static constexpr uint32_t kBand16 = GB::kBand16;          // FP16 kernel only
+  static constexpr uint32_t kBand8 = kDec ? kD2Base + kND2 * kD2Cols : GB::kBand8;
+  static constexpr uint32_t kBand8P2 = kDec ? kBand8 : GB::kBand8P2;
+  static constexpr uint32_t kBand8x16 = kBand8 + (BIG ? 48 : 40);   // wide tile, big window: the band of 16s
   static_assert(!kDec || kBand8 + (WIDE ? 80 : 40) <= kTmemCols, "tensor memory budget");
+  static_assert(!BIG || kBand8x16 + 48 <= kTmemCols, "tensor memory budget");
   static_assert(kND1 <= kMaxRegions && kND2 <= kMaxRegions, "barrier arrays");
 };
 
@@ -166,13 +174,14 @@ __device__ __forceinline__ uint64_t op_desc_k(const OpDesc &d) {
 // Issues the K-steps of one band product: D = A[M=128, K=160] x B[N, K=160]^T
 // with the band A in tensor memory (32 bytes of K = 8 columns per step) and
 // B in shared memory.
-// ACC: the first K-step adds to D instead of overwriting it.
-template <int KIND, int RB, int E, bool ACC = false, int J = 0>
+// ACC: the first K-step adds to D instead of overwriting it.  KS: K-steps per
+// operand byte (5 for K = 160, 6 for the big window's K = 192).
+template <int KIND, int RB, int E, bool ACC = false, int KS = 5, int J = 0>
 __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDesc &b, uint32_t idesc) {
-  if constexpr (J < 5 * E) {
+  if constexpr (J < KS * E) {
     if constexpr (KIND == 0) mma_f16_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, ACC || J > 0);
     else mma_f8f6f4_ts(d, a_tmem + 8 * J, op_desc_k<RB, E, J>(b), idesc, ACC || J > 0);
-    band_mma<KIND, RB, E, ACC, J + 1>(d, a_tmem, b, idesc);
+    band_mma<KIND, RB, E, ACC, KS, J + 1>(d, a_tmem, b, idesc);
   }
 }
 
@@ -190,10 +199,13 @@ __device__ __forceinline__ void band_mma(uint32_t d, uint32_t a_tmem, const OpDe
 // a window stage is one 96-byte x 160-row box (cells x0 - 32 .. x0 + 159),
 // unpacked by the convert warps into the e4m3 operand, and a ring entry is 64
 // bytes x 128 rows (64B swizzle).
-template <int DT, bool ENC, bool SW = false, bool BITS = false, bool WIDE = false, bool NIB = false>
+// BIG: a window stage is 192 x 192 bytes (a 128-column and two 32-column
+// boxes), an H buffer two 128 x 192 digit halves.
+template <int DT, bool ENC, bool SW = false, bool BITS = false, bool WIDE = false, bool NIB = false,
+          bool BIG = false>
 struct Layout {
   static constexpr int E1 = DT == 0 ? 2 : 1;                  // pass-1 operand bytes
-  static constexpr int NS = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);   // TMA window stages
+  static constexpr int NS = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC || BIG) ? 2 : 3);   // TMA window stages
   static constexpr int NR = (SW || BITS || NIB) ? 4 : ((DT == 0 || ENC) ? 2 : 3);  // centre / output ring
   static constexpr int NE = (BITS || NIB) ? 3 : (ENC ? 2 : 1);  // encoded windows (encode ahead)
   // pass-2 operand buffers: FP16 one, so that its two 50 KiB encoded windows
@@ -201,13 +213,13 @@ struct Layout {
   // storage one, for its third encoded window (measured 2% faster)
   static constexpr int NH = SW ? 3 : ((DT == 0 || NIB) ? 1 : 2);
   static constexpr uint32_t kXs = 0;                          // raw windows (TMA)
-  static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : NIB ? 96 * kWin : kWin * Geo<SW>::kRows;  // one window load
+  static constexpr uint32_t kXsBytes = BITS ? 48 * kWin : NIB ? 96 * kWin : BIG ? 192 * 192 : kWin * Geo<SW>::kRows;
   static constexpr uint32_t kXsStride = (kXsBytes + 1023) / 1024 * 1024;  // 128B-swizzle atoms stay aligned
   static constexpr uint32_t kXe = kXs + NS * kXsStride;       // encoded window
   static constexpr uint32_t kXeStride = kWin * kWin * E1;     // one encoded window (25 or 50 KiB)
   static constexpr uint32_t kXeBytes = ENC ? NE * kXeStride : 0;
   static constexpr uint32_t kH = kXe + kXeBytes;              // pass-2 operand (K padded to 160)
-  static constexpr uint32_t kHBytes = kTile * kWin * (SW ? 1 : 2);
+  static constexpr uint32_t kHBytes = kTile * (BIG ? 192 : kWin) * (SW ? 1 : 2);
   static constexpr uint32_t kRing = kH + NH * kHBytes;        // centre tiles / output staging
   static constexpr uint32_t kRingBytes = BITS ? 16 * kTile : NIB ? 64 * kTile : Geo<SW, WIDE>::kTS * Geo<SW, WIDE>::kTS;
   static constexpr uint32_t kBars = kRing + NR * kRingBytes;
@@ -409,10 +421,13 @@ __device__ __forceinline__ uint32_t bytes_to_nib_pairs(uint32_t w) { return w | 
 // kernel keeps its pass-1 band in those 40 columns too: 2^-(k mod 4) at K
 // index k, against window bytes 2^(k mod 4) * 2^-9.  Convert warp (q, kq)
 // writes lanes 32q .. 32q+31 and every other 8-column chunk from chunk kq.
-template <int DT, bool SW, bool WIDE = false, bool FP4 = false, bool BITS = false>
+// The big window holds the e4m3 band and the band of 16s, 48 columns each
+// (K = 192), with offset 32.
+template <int DT, bool SW, bool WIDE = false, bool FP4 = false, bool BITS = false, bool BIG = false>
 __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq, int lane) {
-  using G = Geo<SW, WIDE>;
-  using T = Tm<DT, SW, WIDE>;
+  using G = Geo<SW, WIDE, BIG>;
+  using T = Tm<DT, SW, WIDE, BIG>;
+  constexpr bool W32 = WIDE || BIG;                 // offset 32, the band of 16s second
   // chunks [0, n0) belong to the first band, [n0, n1) to the second, [n1, n)
   // to a third: the f16 band (standard window; the FP16 kernel has only this
   // one) and the e4m3 band, or in the short window the e4m3 bands of pass 1
@@ -421,19 +436,19 @@ __device__ __forceinline__ void store_bands(uint32_t tmem, int r, int q, int kq,
   // on H / 2), the e4m3 band and the e2m1 band (pass 1, after the e4m3 one);
   // the one-bit kernel's pass-1 band sits there too: e4m3 2^-(k mod 4) at
   // column k, against window bytes 2^(k mod 4) * 2^-9 for live cells
-  constexpr int n0 = WIDE ? 5 : (SW ? 5 : 10), n1 = WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
+  constexpr int n0 = BIG ? 6 : WIDE ? 5 : (SW ? 5 : 10), n1 = BIG ? 12 : WIDE ? 10 : (SW ? 10 : (DT == 1 ? 15 : 10));
   constexpr int n = (FP4 || BITS) ? 20 : n1;
   const int m = 32 * q + lane;
   const uint32_t la = static_cast<uint32_t>(32 * q) << 16;
   for (int c = kq; c < n; c += 2) {                 // warp-uniform
     const bool first = c < n0, third = c >= n1;
-    const bool f16 = !SW && !WIDE && first;
+    const bool f16 = !SW && !W32 && first;
     const int cc = first ? c : third ? c - n1 : c - n0;
-    const int off = WIDE ? G::kXOff : (SW && !first) ? G::kYOff : 16;
+    const int off = W32 ? G::kXOff : (SW && !first) ? G::kYOff : 16;
     const uint32_t col = third ? T::kBand8 + 40
-                       : WIDE ? (first ? T::kBand8 : T::kBand8x16)
+                       : W32 ? (first ? T::kBand8 : T::kBand8x16)
                        : SW ? (first ? G::kBand8 : G::kBand8P2) : (first ? G::kBand16 : T::kBand8);
-    const uint32_t one8 = third ? 0x08u : (WIDE && !first) ? 0x58u : 0x38u;   // e2m1 1.0, e4m3 16.0 or 1.0
+    const uint32_t one8 = third ? 0x08u : (W32 && !first) ? 0x58u : 0x38u;   // e2m1 1.0, e4m3 16.0 or 1.0
     const uint32_t one16 = FP4 ? 0x1C00u : 0x3C00u;                             // f16 2^-8 or 1.0
     uint32_t v[8];
 #pragma unroll
@@ -735,7 +750,7 @@ __device__ __forceinline__ int32_t *tile_err(const TcParams &p, int first, int j
 __device__ __forceinline__ bool pass2_f16(int DT, int r) { return DT == 0 || 2 * r + 1 > 15; }
 
 template <int DT, bool ENC, bool BATCH, bool SW, bool BITS, bool MS, bool WIDE = false, bool NIB = false,
-          bool FP4 = false>
+          bool FP4 = false, bool BIG = false>
 __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
   static_assert(!MS || !BATCH, "several steps per launch serve single instances");
   static_assert(!WIDE || (DT == 1 && !ENC && !BATCH && !SW && !BITS && !MS),
@@ -745,14 +760,18 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
                 "four-bit storage runs the FP8 kernel on a re-encoded window, single instance, one step per launch");
   static_assert(!FP4 || (DT == 1 && ENC && !SW && !WIDE && !BATCH && !MS),
                 "FP4 operands: the FP8 kernel on a re-encoded window, single instance, one step per launch");
+  static_assert(!BIG || (DT == 1 && !ENC && !BATCH && !SW && !BITS && !MS && !WIDE && !NIB && !FP4),
+                "the big window serves single two-state instances on FP8 operands, one step per launch");
   static_assert(Layout<DT, ENC, SW, BITS>::NS <= kMaxStages && Layout<DT, ENC, SW, BITS>::NR <= kMaxStages &&
                 Layout<DT, ENC, SW, BITS>::NE <= 3, "barrier arrays");
-  using L = Layout<DT, ENC, SW, BITS, WIDE, NIB>;
+  using L = Layout<DT, ENC, SW, BITS, WIDE, NIB, BIG>;
   // x-coordinate of a tile's centre box in its tensor map (bytes of packed rows)
   auto ctr_x = [](int tx0) { return BITS ? tx0 / 8 : NIB ? tx0 / 2 : tx0; };
-  using G = Geo<SW, WIDE>;
-  using T = Tm<DT, SW, WIDE>;
+  using G = Geo<SW, WIDE, BIG>;
+  using T = Tm<DT, SW, WIDE, BIG>;
   constexpr bool DEC = T::kDec;       // D1 and D2 in separate regions, pass 2 on e4m3 digits
+  constexpr int KW = BIG ? 192 : kWin;   // window columns = pass-1 K = pass-2 K
+  constexpr int KS = KW / 32;            // K-steps of one e4m3 band product
   constexpr int ND1 = T::kND1, ND2 = T::kND2;
   constexpr int E1 = L::E1;
   constexpr int NS = L::NS;
@@ -865,6 +884,8 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         } else {
           tma_load_2d(xs, t.in_a, t.tx0 - G::kXOff, t.ty0 - G::kYOff, &bars->x_full[s]);
           tma_load_2d(xs + G::kRows * 128, t.in_b, t.tx0 - G::kXOff + 128, t.ty0 - G::kYOff, &bars->x_full[s]);
+          if constexpr (BIG)   // columns x0 + 128 .. x0 + 159: the second 32-byte block
+            tma_load_2d(xs + G::kRows * 160, t.in_b, t.tx0 - G::kXOff + 160, t.ty0 - G::kYOff, &bars->x_full[s]);
         }
         issued = j + 1;
       }
@@ -911,7 +932,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         const uint64_t soff = ENC ? (uint64_t)(((j % L::NE) * L::kXeStride) >> 4)   // encoded window
                                   : (uint64_t)((s * L::kXsStride) >> 4);             // window stage
         const OpDesc win{win0.d128 + soff, win0.d32 + soff};
-        band_mma<DT == 0 ? 0 : 1, G::kRows, E1>(tmem + reg * T::kD1Cols, band1, win, idesc1);
+        band_mma<DT == 0 ? 0 : 1, G::kRows, E1, false, KS>(tmem + reg * T::kD1Cols, band1, win, idesc1);
         mma_commit(&bars->d1_full[reg]);
         if (!ENC) mma_commit(&bars->x_empty[s]);   // the raw window is no longer read
       }
@@ -1005,7 +1026,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     // tile's own D1 region.
     if (lane == 0) {
       // the wide tile: N = 96 and f32 accumulators (counts up to 4225)
-      const uint32_t idesc2 = WIDE ? idesc_f32acc(128, G::kTS) : idesc_f16acc(128, kTile);
+      const uint32_t idesc2 = (WIDE || BIG) ? idesc_f32acc(128, G::kTS) : idesc_f16acc(128, kTile);
       const uint32_t band16 = tmem + T::kBand16, band8 = tmem + T::kBand8P2;
       const uint32_t band_hi = tmem + T::kBand8x16;   // wide tile: the band of 16s for the second digit
       const OpDesc hop0 = op_descs(s_base + L::kH);
@@ -1018,7 +1039,14 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         const OpDesc hop{hop0.d128 + hoff, hop0.d32 + hoff};
         const uint32_t d2 = tmem + T::kD2Base + reg * T::kD2Cols;
         const int rj = tile_rule<BATCH>(p, first, j).r;
-        if constexpr (DEC) {
+        if constexpr (BIG) {
+          // the DEC digits at K = 192 into the f32 accumulator over D1's region
+          band_mma<1, kTile, 1, false, 6>(d2, band8, hop, idesc2);
+          if (2 * rj + 1 > 15) {
+            constexpr uint64_t kHi = (uint64_t)((kTile * KW) >> 4);
+            band_mma<1, kTile, 1, true, 6>(d2, band_hi, OpDesc{hop.d128 + kHi, hop.d32 + kHi}, idesc2);
+          }
+        } else if constexpr (DEC) {
           // S = band x (H & 15) + (16 band) x (H >> 4), the second only when H
           // can exceed 15; both e4m3 halves of the H buffer
           band_mma<1, kTile, 1>(d2, band8, hop, idesc2);
@@ -1059,7 +1087,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       off8[c] = op_off(kTile, 1, row, 16 * cc);
     }
     // the bands for the first tile
-    store_bands<DT, SW, WIDE, FP4, BITS>(tmem, r0, q, kq, lane);
+    store_bands<DT, SW, WIDE, FP4, BITS, BIG>(tmem, r0, q, kq, lane);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -1095,7 +1123,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
           if (!ok) break;
         }
         tc_fence_after();
-        store_bands<DT, SW, WIDE, FP4, BITS>(tmem, rj, q, kq, lane);
+        store_bands<DT, SW, WIDE, FP4, BITS, BIG>(tmem, rj, q, kq, lane);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->band_ready);
@@ -1103,7 +1131,38 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       }
       if (!(ok = warp_wait(&bars->d1_full[reg], (j / ND1) & 1, bars, p.timeout_ns))) break;
       tc_fence_after();
-      {
+      if constexpr (BIG) {
+        // D1 (f16 H * 2^-9, 192 columns: six chunks of 16 per warp, read in
+        // two halves of three) -> the e4m3 digits H & 15 and H >> 4 (each
+        // the code of itself times 2^-9) in the two halves of the H buffer,
+        // the second only when H can exceed 15
+        const uint32_t treg = tmem + lane_addr + reg * T::kD1Cols + 96 * kq;
+        uint8_t *hop = smem + L::kH + (j % NH) * L::kHBytes;
+        const bool split = 2 * rj + 1 > 15;
+        const __half2 k512 = __float2half2_rn(512.0f), k1024 = __float2half2_rn(1024.0f);
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t v[3][8];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) tmem_ld16_pack16(treg + 16 * (3 * hf + c), v[c]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            uint32_t e[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k512, k1024)),
+                                 h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k512, k1024)), 0x6420);
+            const uint32_t o = op_off(kTile, 1, row, 16 * (6 * kq + 3 * hf + c));
+            *reinterpret_cast<uint4 *>(hop + o) =
+                make_uint4(e[0] & 0x0F0F0F0Fu, e[1] & 0x0F0F0F0Fu, e[2] & 0x0F0F0F0Fu, e[3] & 0x0F0F0F0Fu);
+            if (split)
+              *reinterpret_cast<uint4 *>(hop + kTile * KW + o) =
+                  make_uint4((e[0] >> 4) & 0x0F0F0F0Fu, (e[1] >> 4) & 0x0F0F0F0Fu, (e[2] >> 4) & 0x0F0F0F0Fu,
+                             (e[3] >> 4) & 0x0F0F0F0Fu);
+          }
+        }
+      } else {
         // D1 is f16 (one value per column); packed loads give f16 pairs, which
         // are already the pass-2 operand (or become e4m3 pairs with one cvt)
         const uint32_t treg = tmem + lane_addr + reg * T::kD1Cols + 80 * kq;
@@ -1167,18 +1226,20 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
       if (ENC && !MS && j + L::NE < n_all && !(ok = encode(j + L::NE, wtid, kCvtThreads))) break;
     }
     if (!ok) set_abort(bars, err0, 8);
-  } else if constexpr (WIDE) {
-    // ------------------------------------- epilogue warps, wide tile (12 .. 27)
+  } else if constexpr (WIDE || BIG) {
+    // ------------------------- epilogue warps, wide tile or big window (12 .. 27)
     // S as f32 (D2, lane y < 96, columns x < 96: six chunks of 16, chunks kq
     // and kq + 4 per warp) and the centre tile (96-byte rows, no swizzle) ->
     // next states in place, stored by TMA.  Warps of lane quarter 3 (rows
-    // 96..127, outside the tile) only take part in the barriers.
+    // 96..127, outside the tile) only take part in the barriers.  Big window:
+    // all 128 rows and eight chunks, the centre tile in the standard
+    // 128B-swizzled ring entry.
     const int q = warp & 3;
     const int kq = (warp - 4 - kCvtWarps) >> 2;
     const int y = 32 * q + lane;
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
-    const bool rows = q < 3;
-    const int nch = kq + 4 < 6 ? 2 : 1;
+    const bool rows = BIG || q < 3;
+    const int nch = (BIG || kq + 4 < 6) ? 2 : 1;
     bool ok = true;
     const IntRule ir = make_int_rule(p.rule);
     TileSeq<false, false, G::kTS> seq(p, first, n_my);
@@ -1203,7 +1264,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
         for (int c = 0; c < nch; ++c) {
           const int cc = kq + 4 * c;
           if (!p.sums) {
-            uint4 *cell = reinterpret_cast<uint4 *>(ring + y * G::kTS + 16 * cc);
+            uint4 *cell = reinterpret_cast<uint4 *>(ring + (BIG ? y * 128 + (((cc ^ y) & 7) << 4) : y * G::kTS + 16 * cc));
             const uint4 cv = *cell;
             uint4 ov;
             ov.x = rule4_binary_i(v[c], cv.x, ir);
@@ -1418,6 +1479,12 @@ __global__ void __launch_bounds__(kThreads, 1) ltl_nib_kernel(const __grid_const
 // instance, FP8 operands, two-state rules, one step per launch.
 __global__ void __launch_bounds__(kThreads, 1) ltl_wide_kernel(const __grid_constant__ TcParams p) {
   ltl_tc_body<1, false, false, false, false, false, true>(p);
+}
+
+// Radii up to 32 on the 128 x 128 tile: the 192 x 192 window, single
+// instance, FP8 operands, two-state rules, one step per launch.
+__global__ void __launch_bounds__(kThreads, 1) ltl_big_kernel(const __grid_constant__ TcParams p) {
+  ltl_tc_body<1, false, false, false, false, false, false, false, false, true>(p);
 }
 
 // Several steps of a single instance in one cooperative launch (separate
@@ -1839,6 +1906,20 @@ cudaError_t wide_launch(const TcParams &p, int grid, cudaStream_t s) {
     configured = true;
   }
   return launch_pdl(tc::ltl_wide_kernel, grid, L::kDyn, s, p);
+}
+
+// The 192 x 192 window: map_in_a / map_in_b are the 128 x 192 and 32 x 192
+// window maps (the second loaded twice, at x0 + 96 and x0 + 128), map_ctr /
+// map_out the 128 x 128 tile maps; tiles_x and n_tiles count 128 x 128 tiles.
+cudaError_t big_launch(const TcParams &p, int grid, cudaStream_t s) {
+  static bool configured = false;
+  using L = tc::Layout<1, false, false, false, false, false, true>;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc::ltl_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kDyn);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  return launch_pdl(tc::ltl_big_kernel, grid, L::kDyn, s, p);
 }
 
 // Simplified von Neumann neighbourhood: FP8, two-state rules, single instance

@@ -92,6 +92,7 @@ std::vector<Cand> candidates(const InstanceInfo &f) {
       out.push_back({CAT_KERNEL_TCGEN05, dt, 128, 160, spl});
       if (f.rule.r <= 7) out.push_back({CAT_KERNEL_TCGEN05, dt, 128, 144, spl});
       out.push_back({CAT_KERNEL_TCGEN05, dt, 96, 0, spl});
+      out.push_back({CAT_KERNEL_TCGEN05, dt, 128, 192, spl});
     }
   }
   out.push_back({CAT_KERNEL_TCGEN05, CAT_DTYPE_FP4_E2M1, 128, 160, 1});

@@ -3,13 +3,15 @@
 Beyond the fragment size the paper extends its scheme with a second halo
 fragment and five band fragments per reduction (Sec. VII); the FP16 fragment
 kernel does that, with FP32 accumulation in step 2 since the counts reach
-65^2 = 4225.  The tcgen05 kernel serves these radii on 96 x 96 output tiles
-inside the same 160 x 160 window (a 32-cell halo; e4m3 operands, the
+65^2 = 4225.  The tcgen05 kernel serves these radii on 128 x 128 output
+tiles inside a 192 x 192 window (a 32-cell halo; e4m3 operands, the
 horizontal sums split into H & 15 and H >> 4 against a band of ones and a
 band of 16s, f32 accumulation in pass 2), which CAT_KERNEL_AUTO picks for
-two-state rules.  The CUDA-core stencil serves these radii too (and the
-simplified von Neumann cross).  cat_set_tile also puts radii up to 16 on the
-96 x 96 tile, and short-window radii on the full window.
+two-state rules, or on 96 x 96 tiles inside the 160 x 160 window
+(cat_set_tile(96, 96)).  The CUDA-core stencil serves these radii too (and
+the simplified von Neumann cross).  cat_set_tile also puts radii up to 16 on
+the 96 x 96 tile or the 192-row window, and short-window radii on the full
+window.
 """
 import numpy as np
 import pytest
@@ -19,8 +21,16 @@ from paper_2406_17284_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [("tcgen05", "fp8"), ("mma_sync", "fp16"), ("stencil", "auto"), ("runsum", "auto"), ("auto", "auto")]
-KIDS = ["tcgen05-fp8", "mma_sync-fp16", "stencil", "runsum", "auto"]
+KERNELS = [("tcgen05", "fp8"), ("tcgen05-96", "fp8"), ("mma_sync", "fp16"), ("stencil", "auto"), ("runsum", "auto"),
+           ("auto", "auto")]
+KIDS = ["tcgen05-fp8", "tcgen05-fp8-tile96", "mma_sync-fp16", "stencil", "runsum", "auto"]
+
+
+def grid_of(cat, H, W, rule, kernel, dtype):
+    """A Grid; "tcgen05-96" is the tcgen05 kernel on the 96 x 96 tile."""
+    if kernel == "tcgen05-96":
+        return cat.Grid(H, W, rule, kernel="tcgen05", dtype=dtype, tile=96)
+    return cat.Grid(H, W, rule, kernel=kernel, dtype=dtype)
 RADII = (17, 20, 24, 31, 32)
 
 
@@ -48,7 +58,7 @@ def assert_same(got, want, what):
 
 
 def run(cat, kernel, dtype, grid, rule, steps):
-    g = cat.Grid(grid.shape[0], grid.shape[1], rule, kernel=kernel, dtype=dtype)
+    g = grid_of(cat, grid.shape[0], grid.shape[1], rule, kernel, dtype)
     try:
         g.set_state(grid)
         g.step(steps)
@@ -65,7 +75,7 @@ def test_counts(cat, kernel, dtype):
     ones = np.ones((200, 230), np.uint8)
     for r in RADII:
         for g_ in (grid, ones):
-            g = cat.Grid(*g_.shape, inputs.scaled_rule(r), kernel=kernel, dtype=dtype)
+            g = grid_of(cat, *g_.shape, inputs.scaled_rule(r), kernel, dtype)
             try:
                 g.set_state(g_)
                 assert_same(g.box_sums(), oracle.box_sums(g_, r), f"S r={r}")
@@ -113,8 +123,10 @@ def test_unsupported(cat):
         assert e.value.code == cat.CAT_ERR_UNSUPPORTED, bad
     g = cat.Grid(64, 64, rule, kernel="tcgen05", dtype="fp8")
     try:
-        for args, code in (((128, 128, 0), cat.CAT_ERR_UNSUPPORTED), ((64, 64, 0), cat.CAT_ERR_INVALID_ARG),
-                           ((96, 96, 150), cat.CAT_ERR_INVALID_ARG), ((96, 96, 144), cat.CAT_ERR_UNSUPPORTED)):
+        for args, code in (((128, 128, 160), cat.CAT_ERR_UNSUPPORTED), ((0, 0, 160), cat.CAT_ERR_UNSUPPORTED),
+                           ((64, 64, 0), cat.CAT_ERR_INVALID_ARG), ((96, 96, 150), cat.CAT_ERR_INVALID_ARG),
+                           ((96, 96, 144), cat.CAT_ERR_UNSUPPORTED), ((96, 96, 192), cat.CAT_ERR_UNSUPPORTED),
+                           ((128, 128, 200), cat.CAT_ERR_INVALID_ARG)):
             with pytest.raises(cat.CatError) as e:
                 cat.cat_set_tile(g.handle, *args)
             assert e.value.code == code, args
@@ -143,15 +155,17 @@ def test_full_4096_sampled_windows(cat):
         a = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8")
         b = cat.Grid(N, N, rule, kernel="stencil", dtype="auto")
         c = cat.Grid(N, N, rule, kernel="mma_sync", dtype="fp16")
+        a96 = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8", tile=96)
         try:
-            for g in (a, b, c):
+            for g in (a, b, c, a96):
                 g.set_state(d)
                 g.step(2)
             torch.cuda.synchronize()
-            assert a.status() == cat.CAT_OK and b.status() == cat.CAT_OK and c.status() == cat.CAT_OK
+            assert all(g.status() == cat.CAT_OK for g in (a, b, c, a96))
             out = a.state_tensor()
-            assert int((out != b.state_tensor()).sum()) == 0, f"r={r}: tcgen05 wide tile and stencil differ"
-            assert int((out != c.state_tensor()).sum()) == 0, f"r={r}: tcgen05 wide tile and fragment kernel differ"
+            assert int((out != b.state_tensor()).sum()) == 0, f"r={r}: tcgen05 192-row window and stencil differ"
+            assert int((out != c.state_tensor()).sum()) == 0, f"r={r}: tcgen05 192-row window and fragment kernel differ"
+            assert int((out != a96.state_tensor()).sum()) == 0, f"r={r}: 192-row window and 96 x 96 tile differ"
             spots = [(0, 0), (0, N - 200), (N - 200, 0), (N - 200, N - 200)] + \
                 [tuple(int(v) for v in rng.integers(0, N - 200, 2)) for _ in range(8)]
             for (y0, x0) in spots:
@@ -163,6 +177,7 @@ def test_full_4096_sampled_windows(cat):
             a.close()
             b.close()
             c.close()
+            a96.close()
 
 
 @pytest.mark.parametrize("r", [1, 5, 8, 13, 16])
@@ -195,3 +210,56 @@ def test_full_window_for_short_window_radii(cat, r):
         assert_same(g.get_state(), oracle.step(grid, orule(rule), n_steps=3), f"r={r}")
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("r", [1, 5, 8, 13, 16])
+def test_big_window_for_small_radii(cat, r):
+    """cat_set_tile(0, 0, 192) on radii up to 16: the 128 x 128 tile in the
+    192 x 192 window, counts and 3 steps vs the oracle on a ragged shape."""
+    grid = inputs.bernoulli(301, 389, 0.45, 950 + r)
+    rule = inputs.scaled_rule(r, M=(r + 1) % 2)
+    g = cat.Grid(301, 389, rule, kernel="tcgen05", dtype="fp8", window=192)
+    try:
+        opts = cat.cat_get_options(g.handle)
+        assert (opts["tile"], opts["window"]) == (128, 192)
+        g.set_state(grid)
+        assert_same(g.box_sums(), oracle.box_sums(grid, r), f"S r={r}")
+        g.step(3)
+        assert g.status() == cat.CAT_OK
+        assert_same(g.get_state(), oracle.step(grid, orule(rule), n_steps=3), f"steps r={r}")
+    finally:
+        g.close()
+
+
+def test_r_above_16_options_and_edges(cat):
+    """Radii above 16 take the 192-row window by default (tile 128) and the
+    96 x 96 tile on request; both agree with the oracle on tiny, one-row,
+    one-column and tile-boundary shapes, all-ones grids (S = 4225 at r = 32)
+    and an impulse."""
+    rule = inputs.scaled_rule(32, M=1)
+    g = cat.Grid(64, 64, rule, kernel="tcgen05", dtype="fp8")
+    try:
+        opts = cat.cat_get_options(g.handle)
+        assert (opts["tile"], opts["window"]) == (128, 192)
+        cat.cat_set_tile(g.handle, 96, 96, 0)
+        opts = cat.cat_get_options(g.handle)
+        assert (opts["tile"], opts["window"]) == (96, 0)
+    finally:
+        g.close()
+    imp = np.zeros((260, 300), np.uint8)
+    imp[130, 150] = 1
+    shapes = [inputs.bernoulli(5, 7, 0.5, 1), inputs.bernoulli(1, 513, 0.5, 2), inputs.bernoulli(513, 1, 0.5, 3),
+              inputs.bernoulli(128, 256, 0.5, 4), inputs.bernoulli(129, 257, 0.5, 5), np.ones((200, 230), np.uint8), imp]
+    for tile in (0, 96):
+        for i, grid in enumerate(shapes):
+            for r in (17, 32):
+                rl = inputs.scaled_rule(r, M=i % 2)
+                g = cat.Grid(*grid.shape, rl, kernel="tcgen05", dtype="fp8", tile=tile)
+                try:
+                    g.set_state(grid)
+                    assert_same(g.box_sums(), oracle.box_sums(grid, r), f"S tile={tile} {grid.shape} r={r}")
+                    g.step(2)
+                    assert g.status() == cat.CAT_OK
+                    assert_same(g.get_state(), oracle.step(grid, orule(rl), n_steps=2), f"tile={tile} {grid.shape} r={r}")
+                finally:
+                    g.close()
