@@ -501,16 +501,18 @@ def measure_multistep(torch, cat, inputs, stream, steps=64):
 
 
 def measure_wide(args, torch, cat, inputs, stream, d_init):
-    """Radii beyond 16 on the headline's grid: the tcgen05 kernel on 96 x 96 tiles
-    (32-cell halo, e4m3 digits against a band of ones and a band of 16s, f32 pass 2),
-    and the FP16 fragment kernel with a second halo fragment (five band fragments
-    per reduction, FP32 step-2 accumulation)."""
+    """Radii beyond 16 on the headline's grid: the tcgen05 kernel on 128 x 128 tiles in
+    a 192 x 192 window (32-cell halo, e4m3 digits against a band of ones and a band of
+    16s, f32 pass 2; the default), the same on 96 x 96 tiles in a 160 x 160 window, and
+    the FP16 fragment kernel with a second halo fragment (five band fragments per
+    reduction, FP32 step-2 accumulation)."""
     n = args.size
-    out = {"workload": f"{n}x{n} bernoulli0.5, scaled rule C2 M1, r > 16: tcgen05 96x96 tile (fp8) "
-                       "and the FP16 fragment kernel", "kernel": "ltl_wide_kernel"}
-    for kern, dt, key in (("tcgen05", "fp8", "tcgen05_fp8"), ("mma_sync", "fp16", "fragment_fp16")):
+    out = {"workload": f"{n}x{n} bernoulli0.5, scaled rule C2 M1, r > 16: tcgen05 (fp8) on 128x128 tiles in a "
+                       "192-row window and on 96x96 tiles, and the FP16 fragment kernel", "kernel": "ltl_big_kernel"}
+    for kern, dt, key, kw in (("tcgen05", "fp8", "tcgen05_fp8", {}), ("tcgen05", "fp8", "tcgen05_fp8_tile96", dict(tile=96)),
+                              ("mma_sync", "fp16", "fragment_fp16", {})):
         for r in (17, 24, 32):
-            g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel=kern, dtype=dt)
+            g = cat.Grid(n, n, inputs.scaled_rule(r, M=1), kernel=kern, dtype=dt, **kw)
             g.set_state(d_init)
             g.step(1, stream)
             t = time_launches(torch, lambda: g.step(1, stream), 3, stream)
