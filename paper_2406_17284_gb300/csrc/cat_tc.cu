@@ -1077,7 +1077,13 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
     const uint32_t lane_addr = static_cast<uint32_t>(32 * q) << 16;
     bool ok = true;
     int band_r = r0;
-    // this thread's operand offsets: D1 column chunks 5kq .. 5kq+4 (16 columns each)
+    // this thread's operand offsets: D1 column chunks 5kq .. 5kq+4 (16 columns
+    // each); the big window's chunks 6kq .. 6kq+5 of its digit operand
+    uint32_t offb[BIG ? 6 : 1];
+    if constexpr (BIG) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) offb[c] = op_off(kTile, 1, row, 16 * (6 * kq + c));
+    }
     uint32_t off16a[5], off16b[5], off8[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -1153,7 +1159,7 @@ __device__ __forceinline__ void ltl_tc_body(const TcParams &p) {
             for (int i = 0; i < 4; ++i)
               e[i] = __byte_perm(h2_bits(__hfma2(as_h2(v[c][2 * i]), k512, k1024)),
                                  h2_bits(__hfma2(as_h2(v[c][2 * i + 1]), k512, k1024)), 0x6420);
-            const uint32_t o = op_off(kTile, 1, row, 16 * (6 * kq + 3 * hf + c));
+            const uint32_t o = offb[3 * hf + c];
             *reinterpret_cast<uint4 *>(hop + o) =
                 make_uint4(e[0] & 0x0F0F0F0Fu, e[1] & 0x0F0F0F0Fu, e[2] & 0x0F0F0F0Fu, e[3] & 0x0F0F0F0Fu);
             if (split)
