@@ -234,7 +234,8 @@ def test_big_window_for_small_radii(cat, r):
 def test_r_above_16_options_and_edges(cat):
     """Radii above 16 take the 192-row window by default (tile 128) and the
     96 x 96 tile on request; both agree with the oracle on tiny, one-row,
-    one-column and tile-boundary shapes, all-ones grids (S = 4225 at r = 32)
+    one-column and tile-boundary shapes, all-ones grids (S = 2025 at r = 22,
+    the largest count the f16 pass 2 holds, 2209 at r = 23, 4225 at r = 32)
     and an impulse."""
     rule = inputs.scaled_rule(32, M=1)
     g = cat.Grid(64, 64, rule, kernel="tcgen05", dtype="fp8")
@@ -252,7 +253,7 @@ def test_r_above_16_options_and_edges(cat):
               inputs.bernoulli(128, 256, 0.5, 4), inputs.bernoulli(129, 257, 0.5, 5), np.ones((200, 230), np.uint8), imp]
     for tile in (0, 96):
         for i, grid in enumerate(shapes):
-            for r in (17, 32):
+            for r in (17, 22, 23, 32):   # 22 / 23: the last f16 and first f32 pass 2 of the 192-row window
                 rl = inputs.scaled_rule(r, M=i % 2)
                 g = cat.Grid(*grid.shape, rl, kernel="tcgen05", dtype="fp8", tile=tile)
                 try:
