@@ -28,6 +28,7 @@ CASES = {
     "bits_r16": (inputs.scaled_rule(16), dict(kernel="tcgen05", dtype="fp8", storage=cat.STORE_BIT1), "ltl_bits_kernel"),
     "wide_r24": (inputs.scaled_rule(24), dict(kernel="tcgen05", dtype="fp8", tile=96), "ltl_wide_kernel"),
     "big_r24": (inputs.scaled_rule(24), dict(kernel="tcgen05", dtype="fp8"), "ltl_big_kernel"),
+    "big_r20": (inputs.scaled_rule(20), dict(kernel="tcgen05", dtype="fp8"), "ltl_big16_kernel"),
     "nib_c16": (inputs.MULTISTATE_R10_C16, dict(kernel="tcgen05", dtype="fp8", storage=cat.STORE_NIB4), "ltl_nib_kernel"),
     "fp4_r16": (inputs.scaled_rule(16), dict(kernel="tcgen05", dtype="fp4"), "ltl_fp4_kernel"),
     "bitslice_r1": (inputs.scaled_rule(1), dict(kernel="bitslice", storage=cat.STORE_BIT1), "ltl_swar_kernel"),
