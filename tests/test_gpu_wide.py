@@ -142,15 +142,16 @@ def test_unsupported(cat):
 
 
 def test_full_4096_sampled_windows(cat):
-    """4096^2 Bernoulli(0.5), r = 24 and 32, two steps of the tcgen05 wide tile
-    checked on 12 windows (corners included) and equal to the stencil and the
-    fragment kernel everywhere."""
+    """4096^2 Bernoulli(0.5), r = 20 (f16 pass 2), 24 and 32, two steps of the
+    tcgen05 192-row window (several tiles per CTA) checked on 12 windows
+    (corners included) and equal to the stencil, the fragment kernel and the
+    96 x 96 tile everywhere."""
     import torch
     N = 4096
     host = inputs.bernoulli(N, N, 0.5, 4242)
     d = torch.from_numpy(host).cuda()
     rng = np.random.default_rng(3)
-    for r in (24, 32):
+    for r in (20, 24, 32):
         rule = inputs.scaled_rule(r)
         a = cat.Grid(N, N, rule, kernel="tcgen05", dtype="fp8")
         b = cat.Grid(N, N, rule, kernel="stencil", dtype="auto")
